@@ -1,0 +1,128 @@
+// Shared device helpers for libdeblur (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace db {
+
+// ---- storage / accumulation types -----------------------------------------
+// Storage T in {double, float, __nv_bfloat16}; arithmetic Acc is double for
+// double storage and float otherwise. Reductions (norms, dot products) are
+// always finished in double.
+template <typename T> struct Traits { using Acc = float; };
+template <> struct Traits<double> { using Acc = double; };
+
+__device__ __forceinline__ float to_acc(float v) { return v; }
+__device__ __forceinline__ double to_acc(double v) { return v; }
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T> __device__ __forceinline__ T from_acc(float v);
+template <> __device__ __forceinline__ float from_acc<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <typename T> __device__ __forceinline__ T from_acc_d(double v);
+template <> __device__ __forceinline__ double from_acc_d<double>(double v) { return v; }
+
+template <typename T, typename A> __device__ __forceinline__ T store_cast(A v);
+template <> __device__ __forceinline__ double store_cast<double, double>(double v) { return v; }
+template <> __device__ __forceinline__ float store_cast<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 store_cast<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+
+__device__ __forceinline__ int wrap(int i, int m) { int r = i % m; return r < 0 ? r + m : r; }
+
+// ---- reductions -------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of NV doubles per thread; result valid in all threads.
+// `scratch` needs NV * 32 doubles of shared memory.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* scratch) {
+  const int lane = threadIdx.x & 31, wid = (threadIdx.x + threadIdx.y * blockDim.x) >> 5;
+  const int nw = (blockDim.x * blockDim.y) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) scratch[k * 32 + wid] = v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = (lane < nw) ? scratch[k * 32 + lane] : 0.0;
+    v[k] = warp_sum(s);
+  }
+  __syncthreads();
+}
+
+// ---- timing / bounded waits ------------------------------------------------
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for cooperative launches, with a time limit. Every block
+// must call it the same number of times. Returns false (in all threads of the
+// block) when the wait timed out or another block already reported a
+// timeout; the caller must then leave the kernel.
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+  int error;      // 0 ok, 1 timeout
+  int decision;   // written by the last block to arrive, read by all after release
+};
+
+// `decide` (if given) runs in the last block to arrive, after every block has
+// finished the phase and before any block is released; its result is
+// returned to all blocks through *decision (no block can start the next phase
+// before it is written).
+template <typename Decide>
+__device__ __forceinline__ bool grid_sync(GridBarrier* gb, unsigned nblocks, uint64_t limit_ns,
+                                          Decide decide, int* decision) {
+  __shared__ int s_ok, s_dec;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    volatile unsigned int* vgen = &gb->gen;
+    volatile int* verr = &gb->error;
+    int ok = (*verr == 0);
+    if (ok) {
+      unsigned my_gen = *vgen;
+      __threadfence();
+      unsigned arrived = atomicAdd(&gb->count, 1u);
+      if (arrived == nblocks - 1) {
+        gb->decision = decide();
+        gb->count = 0;
+        __threadfence();
+        atomicAdd(&gb->gen, 1u);
+      } else {
+        uint64_t t0 = globaltimer_ns();
+        unsigned spins = 0;
+        while (*vgen == my_gen) {
+          if (*verr) { ok = 0; break; }
+          if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > limit_ns) {
+            atomicExch(&gb->error, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      __threadfence();
+      s_dec = *(volatile int*)&gb->decision;
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  if (decision) *decision = s_dec;
+  return s_ok != 0;
+}
+
+struct NoDecision {
+  __device__ int operator()() const { return 0; }
+};
+
+}  // namespace db

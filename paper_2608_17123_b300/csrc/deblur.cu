@@ -1,0 +1,1064 @@
+// libdeblur: host runtime and C-ABI (see include/deblur.h).
+//
+// A solve (Alg. 4) runs entirely on the device: the level hierarchy (bands of
+// every Galerkin coarse operator, restricted right-hand sides), the outer
+// solvers (Alg. 1-3), GCV (Sec. 3) and the transfers (Sec. 4.1). The host
+// only sequences launches and reads one small status record per outer
+// iteration (LSQR iteration count and the two RC norms) to take the stopping
+// decision of Eq. (stop).
+#include <cuda_runtime.h>
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "../../include/deblur.h"
+#include "gcv.cuh"
+
+using namespace db;
+
+// ============================================================================
+// error plumbing
+// ============================================================================
+struct DbError {
+  db_status st;
+  std::string msg;
+};
+
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      cudaGetLastError();                                                         \
+      throw DbError{DB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    }                                                                             \
+  } while (0)
+
+#define REQUIRE(cond, text) \
+  do { if (!(cond)) throw DbError{DB_EINVAL, text}; } while (0)
+
+static thread_local std::string g_last_error;
+
+// ============================================================================
+// device arena owned by a context
+// ============================================================================
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0, off = 0;
+  size_t budget = 0;
+  void reset() { off = 0; }
+  void ensure(size_t bytes) {
+    if (bytes <= cap) return;
+    if (budget && bytes > budget) throw DbError{DB_ENOMEM, "workspace exceeds the context's HBM budget"};
+    if (base) cudaFree(base);
+    base = nullptr;
+    cap = 0;
+    if (cudaMalloc(&base, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      throw DbError{DB_ENOMEM, "cudaMalloc of the workspace failed"};
+    }
+    cap = bytes;
+  }
+  template <typename X> X* take(size_t count) {
+    size_t bytes = (count * sizeof(X) + 255) & ~size_t(255);
+    if (off + bytes > cap) throw DbError{DB_ENOMEM, "workspace arena exhausted"};
+    X* p = reinterpret_cast<X*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+struct db_context {
+  int device = 0;
+  int nsm = 0;
+  Arena arena;
+  std::string err;
+  db_stats stats{};
+  int profiling = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+// Every kernel launch of the library is preceded by count_launch() so the
+// context can report how many of its kernels ran.
+static thread_local db_context* g_count_ctx = nullptr;
+static inline void count_launch() {
+  if (g_count_ctx) g_count_ctx->stats.kernel_launches++;
+}
+struct CountScope {
+  db_context* prev;
+  explicit CountScope(db_context* c) : prev(g_count_ctx) { g_count_ctx = c; }
+  ~CountScope() { g_count_ctx = prev; }
+};
+
+
+static Filter make_filter(db_wavelet wv) {
+  Filter f{};
+  if (wv == DB_HAAR) {
+    f.kappa = 2;
+    f.h[0] = f.h[1] = std::sqrt(2.0) / 2.0;
+  } else {
+    const double s3 = std::sqrt(3.0), d = 4.0 * std::sqrt(2.0);
+    f.kappa = 4;
+    f.h[0] = (1 + s3) / d; f.h[1] = (3 + s3) / d; f.h[2] = (3 - s3) / d; f.h[3] = (1 - s3) / d;
+  }
+  return f;
+}
+
+static int grid_for(size_t n, int nsm, int per = 256) {
+  size_t g = (n + per - 1) / per;
+  size_t cap = (size_t)nsm * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// ============================================================================
+// level hierarchy
+// ============================================================================
+template <typename T>
+struct Level {
+  using Acc = typename Traits<T>::Acc;
+  int m = 0;
+  size_t n = 0;
+  int dlo = 0, w = 0;
+  double* Bd_r = nullptr;    // double bands [t][m][w]
+  double* Bd_c = nullptr;
+  Acc *br = nullptr, *bc = nullptr, *brT = nullptr, *bcT = nullptr;
+  float* rho = nullptr;      // GCV symbol ratios [n]
+  // vectors
+  T* b = nullptr;
+  T* xa = nullptr;
+  T* xb = nullptr;
+  T *uA = nullptr, *uLx = nullptr, *uLy = nullptr, *v = nullptr, *wv = nullptr, *dlt = nullptr;
+  T *a0x = nullptr, *a0y = nullptr, *a1x = nullptr, *a1y = nullptr;
+  int ntiles_side() const { return (m + TM - 1) / TM; }
+  BandOp<Acc> op(int nterms) const {
+    BandOp<Acc> o;
+    o.m = m; o.nterms = nterms; o.dlo = dlo; o.w = w;
+    o.br = br; o.bc = bc; o.brT = brT; o.bcT = bcT;
+    return o;
+  }
+};
+
+static void coarse_band_shape(int m_c, int dlo, int w, int kappa, int* dlo2, int* w2) {
+  // nonzero offsets of the coarse factor: [ceil((dlo-(kappa-1))/2), floor((dlo+w-1+kappa-1)/2)]
+  int lo = (int)std::ceil((dlo - (kappa - 1)) / 2.0);
+  int hi = (int)std::floor((dlo + w - 1 + kappa - 1) / 2.0);
+  if (hi - lo + 1 >= m_c) { *dlo2 = -(m_c / 2); *w2 = m_c; }
+  else { *dlo2 = lo; *w2 = hi - lo + 1; }
+}
+
+template <typename T>
+struct Hierarchy {
+  using Acc = typename Traits<T>::Acc;
+  int nterms = 0, S = 0, levels = 0;
+  std::vector<Level<T>> lv;
+};
+
+template <typename T>
+__global__ void k_convert_in(size_t n, const double* __restrict__ x, T* __restrict__ y) {
+  using Acc = typename Traits<T>::Acc;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = store_cast<T, Acc>((Acc)x[i]);
+}
+template <typename T>
+__global__ void k_convert_out(size_t n, const T* __restrict__ x, double* __restrict__ y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (double)to_acc(x[i]);
+}
+template <typename T>
+__global__ void k_fill(size_t n, T* __restrict__ y, double v) {
+  using Acc = typename Traits<T>::Acc;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = store_cast<T, Acc>((Acc)v);
+}
+
+// ============================================================================
+// the solver for one storage type
+// ============================================================================
+template <typename T>
+struct Engine {
+  using Acc = typename Traits<T>::Acc;
+  db_context* ctx;
+  cudaStream_t st;
+  Hierarchy<T> H;
+  db_opts o;
+  db_gcv_opts go;
+  // scratch shared by all levels
+  double* d_part = nullptr;
+  size_t part_cap = 0;
+  unsigned* d_cnt = nullptr;
+  double* d_box = nullptr;           // small device mailbox
+  GridBarrier* d_gb = nullptr;
+  LsqrState* d_st = nullptr;
+  LsqrProb<T, Acc>* d_prob = nullptr;
+  int* d_tile_prob = nullptr;
+  // GCV workspace
+  Acc* gV = nullptr;
+  Acc *gt = nullptr, *gz = nullptr, *gy = nullptr, *gatb = nullptr, *gdtc = nullptr, *gknext = nullptr;
+  Acc *gcx = nullptr, *gcy = nullptr;
+  double *gGA = nullptr, *gGD = nullptr, *ggA = nullptr, *ggD = nullptr, *gh = nullptr, *gwork = nullptr;
+  double* gmdot_part = nullptr;
+  int gkmax = 0;
+  size_t gn = 0;
+
+  Engine(db_context* c, cudaStream_t s) : ctx(c), st(s) {}
+
+  // ---------------------------------------------------------------- setup
+  static size_t footprint(int m, int levels, int S, const db_gcv_opts& g) {
+    size_t tot = 0;
+    const int kmax = std::max(g.proj_dim_max, g.proj_dim) + 2;
+    size_t n0 = (size_t)m * m;
+    for (int i = 0; i < levels; ++i) {
+      int mi = m >> i;
+      size_t n = (size_t)mi * mi;
+      tot += n * sizeof(T) * 16 + n * sizeof(float);
+      tot += (size_t)mi * (S + 64) * (sizeof(double) * 2 + sizeof(Acc) * 4) * S + 4096;
+    }
+    tot += n0 * sizeof(Acc) * (kmax + 9);
+    tot += (size_t)kmax * kmax * sizeof(double) * 6 + (size_t)kmax * 4096 * sizeof(double);
+    tot += 64ull << 20;
+    return tot;
+  }
+
+  void build(const double* psf_dev, int S, int m, int levels, db_wavelet wv, const double* b_dev, bool with_vectors) {
+    Arena& A = ctx->arena;
+    H.S = S;
+    H.levels = levels;
+    H.lv.assign(levels, Level<T>());
+    // PSF factorisation (rank-revealing one-sided Jacobi SVD)
+    double* fr = A.take<double>((size_t)S * S);
+    double* fc = A.take<double>((size_t)S * S);
+    double* wk = A.take<double>((size_t)2 * S * S + S);
+    int* d_nt = A.take<int>(1);
+    { count_launch(); k_psf_svd<<<1, 128, 0, st>>>(S, psf_dev, 1e-13, d_nt, fr, fc, wk); }
+    CK(cudaGetLastError());
+    int nterms = 0;
+    CK(cudaMemcpyAsync(&nterms, d_nt, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    REQUIRE(nterms >= 1, "PSF is zero");
+    H.nterms = nterms;
+    const Filter f = make_filter(wv);
+    const int kmax = std::max(go.proj_dim_max, go.proj_dim) + 2;
+    for (int i = 0; i < levels; ++i) {
+      Level<T>& L = H.lv[i];
+      L.m = m >> i;
+      L.n = (size_t)L.m * L.m;
+      if (i == 0) { L.dlo = -(S / 2); L.w = S; }
+      else coarse_band_shape(L.m, H.lv[i - 1].dlo, H.lv[i - 1].w, f.kappa, &L.dlo, &L.w);
+      REQUIRE(L.w <= MAX_BAND, "coarse operator band too wide for the tile kernels");
+      size_t nb = (size_t)nterms * L.m * L.w;
+      L.Bd_r = A.take<double>(nb);
+      L.Bd_c = A.take<double>(nb);
+      L.br = A.take<Acc>(nb); L.bc = A.take<Acc>(nb); L.brT = A.take<Acc>(nb); L.bcT = A.take<Acc>(nb);
+      const int gb = grid_for(nb, ctx->nsm);
+      if (i == 0) {
+        { count_launch(); k_fine_bands_d<<<gb, 256, 0, st>>>(L.m, S, nterms, fr, L.Bd_r); }
+        { count_launch(); k_fine_bands_d<<<gb, 256, 0, st>>>(L.m, S, nterms, fc, L.Bd_c); }
+      } else {
+        const Level<T>& P = H.lv[i - 1];
+        { count_launch(); k_coarsen_bands<<<gb, 256, 0, st>>>(P.m, P.dlo, P.w, nterms, f, P.Bd_r, L.dlo, L.w, L.Bd_r); }
+        { count_launch(); k_coarsen_bands<<<gb, 256, 0, st>>>(P.m, P.dlo, P.w, nterms, f, P.Bd_c, L.dlo, L.w, L.Bd_c); }
+      }
+      { count_launch(); k_transpose_band<Acc><<<gb, 256, 0, st>>>(L.m, L.dlo, L.w, nterms, L.Bd_r, L.br, L.brT); }
+      { count_launch(); k_transpose_band<Acc><<<gb, 256, 0, st>>>(L.m, L.dlo, L.w, nterms, L.Bd_c, L.bc, L.bcT); }
+      CK(cudaGetLastError());
+      if (with_vectors) {
+        const size_t n = L.n;
+        L.rho = A.take<float>(n);
+        double2* Kr = A.take<double2>((size_t)nterms * L.m);
+        double2* Kc = A.take<double2>((size_t)nterms * L.m);
+        const int g1 = grid_for((size_t)nterms * L.m, ctx->nsm);
+        { count_launch(); k_band_dft<<<g1, 256, 0, st>>>(L.m, L.dlo, L.w, nterms, L.Bd_r, Kr); }
+        { count_launch(); k_band_dft<<<g1, 256, 0, st>>>(L.m, L.dlo, L.w, nterms, L.Bd_c, Kc); }
+        { count_launch(); k_symbol_rho<<<grid_for(n, ctx->nsm), 256, 0, st>>>(L.m, nterms, Kr, Kc, L.rho); }
+        CK(cudaGetLastError());
+        L.b = A.take<T>(n);
+        L.xa = A.take<T>(n); L.xb = A.take<T>(n);
+        L.uA = A.take<T>(n); L.uLx = A.take<T>(n); L.uLy = A.take<T>(n);
+        L.v = A.take<T>(n); L.wv = A.take<T>(n); L.dlt = A.take<T>(n);
+        L.a0x = A.take<T>(n); L.a0y = A.take<T>(n); L.a1x = A.take<T>(n); L.a1y = A.take<T>(n);
+      }
+    }
+    if (with_vectors && b_dev) {
+      const size_t n0 = H.lv[0].n;
+      { count_launch(); k_convert_in<T><<<grid_for(n0, ctx->nsm), 256, 0, st>>>(n0, b_dev, H.lv[0].b); }
+      for (int i = 1; i < levels; ++i) {
+        const Level<T>& P = H.lv[i - 1];
+        { count_launch(); k_restrict<T><<<grid_for(H.lv[i].n, ctx->nsm), 256, 0, st>>>(P.m, f, P.b, H.lv[i].b); }
+      }
+      CK(cudaGetLastError());
+    }
+    // shared scratch
+    const size_t n0 = (size_t)m * m;
+    size_t ntiles = 0;
+    for (auto& L : H.lv) ntiles = std::max(ntiles, (size_t)L.ntiles_side() * L.ntiles_side());
+    part_cap = std::max<size_t>(ntiles * 3 + 64, 8192);
+    d_part = A.take<double>(part_cap);
+    d_cnt = A.take<unsigned>(64);
+    d_box = A.take<double>(64);
+    d_gb = A.take<GridBarrier>(1);
+    d_st = A.take<LsqrState>(1);
+    d_prob = A.take<LsqrProb<T, Acc>>(1);
+    d_tile_prob = A.take<int>(ntiles + 1);
+    CK(cudaMemsetAsync(d_cnt, 0, 64 * sizeof(unsigned), st));
+    CK(cudaMemsetAsync(d_gb, 0, sizeof(GridBarrier), st));
+    if (with_vectors) {
+      gkmax = kmax;
+      gn = n0;
+      gV = A.take<Acc>((size_t)kmax * n0);
+      gt = A.take<Acc>(n0); gz = A.take<Acc>(n0); gy = A.take<Acc>(n0);
+      gatb = A.take<Acc>(n0); gdtc = A.take<Acc>(n0); gknext = A.take<Acc>(n0);
+      gcx = A.take<Acc>(n0); gcy = A.take<Acc>(n0);
+      gGA = A.take<double>((size_t)kmax * kmax);
+      gGD = A.take<double>((size_t)kmax * kmax);
+      ggA = A.take<double>(kmax);
+      ggD = A.take<double>(kmax);
+      gh = A.take<double>(kmax);
+      gwork = A.take<double>((size_t)3 * kmax * kmax + 8 * kmax);
+      gmdot_part = A.take<double>((size_t)kmax * 256);
+    }
+  }
+
+  // ---------------------------------------------------------------- operators
+  int smem_bytes(const BandOp<Acc>& op) const {
+    TileGeom g = tile_geom(op, false), gt = tile_geom(op, true);
+    return std::max(tile_smem_elems(g.H, g.w), tile_smem_elems(gt.H, gt.w)) * (int)sizeof(Acc);
+  }
+
+  void blur(const Level<T>& L, bool tr, const Acc* x, Acc* y, Acc scale = Acc(1)) {
+    BandOp<Acc> op = L.op(H.nterms);
+    const int sm = smem_bytes(op);
+    if (sm > 48 * 1024) CK(cudaFuncSetAttribute(k_blur<Acc, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    const int nt = L.ntiles_side();
+    const int grid = std::min(nt * nt, ctx->nsm * 8);
+    { count_launch(); k_blur<Acc, Acc><<<grid, dim3(32, TY), sm, st>>>(op, tr ? 1 : 0, x, y, scale); }
+    CK(cudaGetLastError());
+  }
+
+  void blur_T(const Level<T>& L, bool tr, const T* x, T* y) {
+    BandOp<Acc> op = L.op(H.nterms);
+    const int sm = smem_bytes(op);
+    if (sm > 48 * 1024) CK(cudaFuncSetAttribute(k_blur<T, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    const int nt = L.ntiles_side();
+    const int grid = std::min(nt * nt, ctx->nsm * 8);
+    { count_launch(); k_blur<T, Acc><<<grid, dim3(32, TY), sm, st>>>(op, tr ? 1 : 0, x, y, Acc(1)); }
+    CK(cudaGetLastError());
+  }
+
+  double dot(size_t n, const Acc* x, const Acc* y) {
+    const int g = grid_for(n, ctx->nsm);
+    { count_launch(); k_dot<Acc, Acc><<<g, 256, 0, st>>>(n, x, y, d_part, d_cnt + 8, d_box + 8); }
+    CK(cudaGetLastError());
+    double v;
+    CK(cudaMemcpyAsync(&v, d_box + 8, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return v;
+  }
+  template <typename X>
+  void dot_dev(size_t n, const X* x, const X* y, double* out) {
+    const int g = grid_for(n, ctx->nsm);
+    { count_launch(); k_dot<X, X><<<g, 256, 0, st>>>(n, x, y, d_part, d_cnt + 9, out); }
+    CK(cudaGetLastError());
+  }
+
+  // ---------------------------------------------------------------- LSQR
+  int lsqr(const Level<T>& L, int solver, double gamma, const T* x0, int* stop_out = nullptr) {
+    LsqrProb<T, Acc> P;
+    P.op = L.op(H.nterms);
+    P.m = L.m;
+    P.solver = solver;
+    P.gamma = gamma;
+    P.b = L.b;
+    P.x0 = x0;
+    P.a0x = L.a0x; P.a0y = L.a0y; P.a1x = L.a1x; P.a1y = L.a1y;
+    P.uA = L.uA; P.uLx = L.uLx; P.uLy = L.uLy; P.v = L.v; P.w = L.wv; P.dlt = L.dlt;
+    P.nt = L.ntiles_side();
+    P.ntiles = P.nt * P.nt;
+    P.tile_begin = 0;
+    CK(cudaMemcpyAsync(d_prob, &P, sizeof(P), cudaMemcpyHostToDevice, st));
+    std::vector<int> tp(P.ntiles, 0);
+    CK(cudaMemcpyAsync(d_tile_prob, tp.data(), sizeof(int) * tp.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(d_st, 0, sizeof(LsqrState), st));
+    CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned), st));
+    CK(cudaMemsetAsync(d_gb, 0, sizeof(GridBarrier), st));
+    LsqrCtl c;
+    c.atol = o.lsqr_atol; c.btol = o.lsqr_btol; c.conlim = o.lsqr_conlim; c.maxit = o.lsqr_maxit;
+    c.nprob = 1; c.ntiles = P.ntiles;
+    c.tile_prob = d_tile_prob; c.part = d_part; c.cnt = d_cnt; c.st = d_st; c.gb = d_gb;
+    c.limit_ns = 2000000000ull;
+    const int sm = smem_bytes(P.op);
+    auto kfn = k_lsqr<T, Acc>;
+    if (sm > 48 * 1024) CK(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, sm));
+    REQUIRE(per_sm >= 1, "LSQR kernel does not fit on an SM");
+    const int grid = std::max(1, std::min(P.ntiles, per_sm * ctx->nsm));
+    const LsqrProb<T, Acc>* pp = d_prob;
+    void* args[] = {(void*)&pp, (void*)&c};
+    if (ctx->profiling) CK(cudaEventRecord(ctx->ev0, st));
+    count_launch();
+    CK(cudaLaunchCooperativeKernel((const void*)kfn, dim3(grid), dim3(32, TY), args, sm, st));
+    if (ctx->profiling) CK(cudaEventRecord(ctx->ev1, st));
+    LsqrState S;
+    GridBarrier gbh;
+    CK(cudaMemcpyAsync(&S, d_st, sizeof(S), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&gbh, d_gb, sizeof(gbh), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (gbh.error) throw DbError{DB_ETIMEOUT, "LSQR grid barrier timed out"};
+    if (stop_out) *stop_out = S.stop;
+    ctx->stats.lsqr_launches++;
+    const double pix = (double)(S.its + 1) * (double)L.n;
+    if (solver == DB_IRLS) ctx->stats.lsqr_pixel_iters_irls += pix;
+    else ctx->stats.lsqr_pixel_iters_other += pix;
+    if (ctx->profiling) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+      ctx->stats.lsqr_ms += ms;
+    }
+    return S.its;
+  }
+
+  // ---------------------------------------------------------------- GCV
+  void mdot(size_t n, int nvec, const Acc* V, const Acc* y, double* out, int ostride) {
+    int nch = (int)std::min<size_t>(256, (n + 2047) / 2048);
+    nch = std::max(nch, 1);
+    { count_launch(); k_mdot<Acc><<<dim3(nch, nvec), 256, 0, st>>>(n, nvec, V, n, y, gmdot_part); }
+    { count_launch(); k_mdot_reduce<<<(nvec + 7) / 8, 256, 0, st>>>(nvec, nch, gmdot_part, out, ostride); }
+    CK(cudaGetLastError());
+  }
+  void maxpy(size_t n, int nvec, const Acc* V, const double* h, int hstride, Acc* y) {
+    { count_launch(); k_maxpy<Acc><<<grid_for(n, ctx->nsm), 256, 0, st>>>(n, nvec, V, n, h, hstride, y); }
+    CK(cudaGetLastError());
+  }
+
+  // column j of the Gram matrices for basis vector V_j (all V_0..V_j present)
+  void gram_column(const Level<T>& L, int j, const T* wx, const T* wy, bool has_c) {
+    const size_t n = L.n;
+    const int ld = gkmax;
+    Acc* vj = gV + (size_t)j * n;
+    blur(L, false, vj, gz);
+    blur(L, true, gz, gt);
+    { count_launch(); k_DtD<Acc, T><<<grid_for(n, ctx->nsm), 256, 0, st>>>(L.m, vj, wx, wy, gy); }
+    CK(cudaGetLastError());
+    // G[i][j] for i <= j stored at G[i*ld + j]
+    mdot(n, j + 1, gV, gt, gGA + j, ld);
+    mdot(n, j + 1, gV, gy, gGD + j, ld);
+    mdot(n, 1, vj, gatb, ggA + j, 1);
+    if (has_c) mdot(n, 1, vj, gdtc, ggD + j, 1);
+    else CK(cudaMemsetAsync(ggD + j, 0, sizeof(double), st));
+  }
+
+  double gcv(const Level<T>& L, int solver, bool weighted, bool shifted) {
+    if (go.gamma_fixed > 0) return go.gamma_fixed;
+    ctx->stats.gcv_calls++;
+    const size_t n = L.n;
+    const int m = L.m;
+    const int ld = gkmax;
+    const int gsz = grid_for(n, ctx->nsm);
+    const T* wx = weighted ? L.a0x : nullptr;
+    const T* wy = weighted ? L.a0y : nullptr;
+    // A^T b, ||b||^2
+    { count_launch(); k_to_acc<T, Acc><<<gsz, 256, 0, st>>>(n, L.b, (const T*)nullptr, gz); }
+    CK(cudaGetLastError());
+    const double bnorm2 = dot(n, gz, gz);
+    blur(L, true, gz, gatb);
+    const double atb2 = dot(n, gatb, gatb);
+    // D^T c
+    bool has_c = false;
+    if (shifted) {
+      { count_launch(); k_to_acc<T, Acc><<<gsz, 256, 0, st>>>(n, L.a0x, solver == 2 ? L.a1x : nullptr, gcx); }
+      { count_launch(); k_to_acc<T, Acc><<<gsz, 256, 0, st>>>(n, L.a0y, solver == 2 ? L.a1y : nullptr, gcy); }
+      { count_launch(); k_Lt_w<Acc, T><<<gsz, 256, 0, st>>>(m, gcx, gcy, (const T*)nullptr, (const T*)nullptr, gdtc); }
+      CK(cudaGetLastError());
+      has_c = dot(n, gdtc, gdtc) > 0.0;
+    }
+    double s = 1.0;
+    if (weighted) {
+      double* box = d_box + 16;
+      dot_dev<T>(n, L.a0x, L.a0x, box);
+      dot_dev<T>(n, L.a0y, L.a0y, box + 1);
+      double h2[2];
+      CK(cudaMemcpyAsync(h2, box, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      s = (h2[0] + h2[1]) / (2.0 * m * (m - 1));
+    }
+    // v_0
+    CK(cudaMemcpyAsync(d_box + 20, &atb2, sizeof(double), cudaMemcpyHostToDevice, st));
+    { count_launch(); k_scale_inv_sqrt<Acc><<<gsz, 256, 0, st>>>(n, gatb, d_box + 20, gV); }
+    CK(cudaGetLastError());
+    const double dtc_norm2 = has_c ? dot(n, gdtc, gdtc) : 0.0;
+    int nK = 1;            // Krylov vectors materialised in gV
+    int cols = 0;          // Krylov columns computed
+    bool pending = false;  // gknext holds an unnormalised next Krylov vector
+    bool broke = false;
+    const int kcap = (int)std::min<size_t>((size_t)go.proj_dim_max, n);
+    int kdim = std::min<int>(go.proj_dim, kcap);
+    double gamma_prev = -1.0, gamma = 0.0;
+    const bool check_breakdown = n <= 4096;
+    for (;;) {
+      // extend the Krylov basis to kdim vectors with their Gram columns
+      while (cols < kdim && !broke) {
+        if (cols == nK) {
+          if (!pending) break;
+          { count_launch(); k_scale_inv_sqrt<Acc><<<gsz, 256, 0, st>>>(n, gknext, d_box + 21, gV + (size_t)nK * n); }
+          CK(cudaGetLastError());
+          ++nK;
+          pending = false;
+        }
+        const int j = cols;
+        gram_column(L, j, wx, wy, has_c);
+        ++cols;
+        if (cols < kdim || cols < kcap) {
+          // next direction: t = A^T A v_j orthogonalised against V_0..V_j, twice
+          // (first pass reuses the Gram column: G_A[i][j] = V_i . t)
+          CK(cudaMemcpyAsync(gknext, gt, n * sizeof(Acc), cudaMemcpyDeviceToDevice, st));
+          maxpy(n, j + 1, gV, gGA + j, ld, gknext);
+          mdot(n, j + 1, gV, gknext, gh, 1);
+          maxpy(n, j + 1, gV, gh, 1, gknext);
+          dot_dev<Acc>(n, gknext, gknext, d_box + 21);
+          pending = true;
+          if (check_breakdown) {
+            double nt2;
+            CK(cudaMemcpyAsync(&nt2, d_box + 21, sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (std::sqrt(nt2) <= 1e-12 * std::sqrt(atb2)) { broke = true; pending = false; }
+          }
+        }
+      }
+      int kk = cols;
+      // shift direction orth(D^T c) in slot kk
+      if (has_c) {
+        Acc* vc = gV + (size_t)kk * n;
+        CK(cudaMemcpyAsync(vc, gdtc, n * sizeof(Acc), cudaMemcpyDeviceToDevice, st));
+        for (int pass = 0; pass < 2; ++pass) {
+          mdot(n, kk, gV, vc, gh, 1);
+          maxpy(n, kk, gV, gh, 1, vc);
+        }
+        const double nc2 = dot(n, vc, vc);
+        if (std::sqrt(nc2) > 1e-12 * std::sqrt(dtc_norm2)) {
+          CK(cudaMemcpyAsync(d_box + 22, &nc2, sizeof(double), cudaMemcpyHostToDevice, st));
+          { count_launch(); k_scale_inv_sqrt<Acc><<<gsz, 256, 0, st>>>(n, vc, d_box + 22, vc); }
+          CK(cudaGetLastError());
+          gram_column(L, kk, wx, wy, true);
+          ++kk;
+        }
+      }
+      // small problem + selection
+      GcvSelectArgs a;
+      a.kk = kk; a.ld = ld; a.GA = gGA; a.GD = gGD; a.gA = ggA; a.gD = ggD;
+      a.bnorm2 = bnorm2; a.n = (double)n; a.s = s; a.rho = L.rho; a.npix = (int)n;
+      a.lo = go.log10_gamma_lo; a.hi = go.log10_gamma_hi; a.tolx = go.refine_tol_log10;
+      a.npts = go.grid_points; a.max_ext = 2; a.work = gwork; a.out = d_box + 24;
+      { count_launch(); k_gcv_select<<<1, SEL_THREADS, 0, st>>>(a); }
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(&gamma, d_box + 24, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (gamma_prev > 0 && std::fabs(gamma - gamma_prev) <= 1e-3 * gamma_prev) return gamma;
+      if (2 * kdim > kcap || kdim >= (int)n || broke) return gamma;
+      gamma_prev = gamma;
+      kdim *= 2;
+    }
+  }
+
+  // ---------------------------------------------------------------- outer step
+  // x_new = x_old + delta, auxiliaries from L x_new; returns RC.
+  double outer_update(Level<T>& L, int solver, const T* x_old, T* x_new) {
+    const size_t n = L.n;
+    const int g = grid_for(n, ctx->nsm);
+    { count_launch(); k_outer_update<T><<<g, 256, 0, st>>>(L.m, solver, o.lsqr_warm_start, x_old, L.dlt, x_new, L.a0x, L.a0y,
+                                         L.a1x, L.a1y, o.eps_irls, o.eps_mm, o.tau_sb, d_part, d_cnt + 4, d_box); }
+    CK(cudaGetLastError());
+    double h[2];
+    CK(cudaMemcpyAsync(h, d_box, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return h[1] == 0.0 ? INFINITY : std::sqrt(h[0]) / std::sqrt(h[1]);
+  }
+
+  // one level of Alg. 4 (Alg. 1/2/3 inside); x in L.xa on entry and exit
+  void level_solve(Level<T>& L, int solver, double tol, bool twopass, double* mu, int* iters, int* inner) {
+    T* x = L.xa;
+    T* xn = L.xb;
+    double gamma = 0.0;
+    int k = 0, tot_inner = 0;
+    for (k = 0; k < o.kmax; ++k) {
+      if (solver == DB_IRLS) {
+        if (!twopass) gamma = gcv(L, solver, true, false);
+        else if (k == 0) gamma = gcv(L, solver, false, false);
+        else if (k == 3) gamma = gcv(L, solver, true, false);
+      } else if (k < go.gcv_estimates) {
+        gamma = gcv(L, solver, false, true);
+      }
+      const int its = lsqr(L, solver, gamma, o.lsqr_warm_start ? x : nullptr);
+      tot_inner += its;
+      ctx->stats.outer_iterations++;
+      const double rc = outer_update(L, solver, x, xn);
+      std::swap(x, xn);
+      if (rc < tol) { ++k; break; }
+    }
+    if (k > o.kmax) k = o.kmax;
+    if (x != L.xa) CK(cudaMemcpyAsync(L.xa, x, L.n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    *mu = gamma;
+    *iters = k;
+    *inner = tot_inner;
+  }
+
+  void vcycle(db_solver solver, db_wavelet wv, db_transfer tr, double* mu, int* iters, int* inner) {
+    const Filter f = make_filter(wv);
+    const int levels = H.levels;
+    for (int i = levels - 1; i >= 0; --i) {
+      Level<T>& L = H.lv[i];
+      const int g = grid_for(L.n, ctx->nsm);
+      if (i == levels - 1) {
+        { count_launch(); k_fill<T><<<g, 256, 0, st>>>(L.n, L.xa, 0.0); }
+        { count_launch(); k_aux_init<T><<<g, 256, 0, st>>>(L.m, solver, AUX_APPROACH_I, L.xa, L.a0x, L.a0y, L.a1x, L.a1y,
+                                          o.eps_irls, o.eps_mm, o.tau_sb); }
+      } else {
+        const Level<T>& C = H.lv[i + 1];
+        if (tr == DB_APPROACH_X) {
+          { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.xa, L.xa, 0, 0); }
+          { count_launch(); k_aux_init<T><<<g, 256, 0, st>>>(L.m, solver, AUX_FROM_X, L.xa, L.a0x, L.a0y, L.a1x, L.a1y,
+                                            o.eps_irls, o.eps_mm, o.tau_sb); }
+        } else {
+          { count_launch(); k_fill<T><<<g, 256, 0, st>>>(L.n, L.xa, 0.0); }
+          { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.a0x, L.a0x, 1, 0); }
+          { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.a0y, L.a0y, 0, 1); }
+          if (solver == DB_SB) {
+            { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.a1x, L.a1x, 1, 0); }
+            { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.a1y, L.a1y, 0, 1); }
+          }
+        }
+      }
+      CK(cudaGetLastError());
+      const double tol = i > 0 ? o.tol_coarse : o.tol_fine;
+      const bool twopass = (solver == DB_IRLS && levels >= 3 && i == 0);
+      level_solve(L, solver, tol, twopass, &mu[i], &iters[i], &inner[i]);
+    }
+  }
+};
+
+// ============================================================================
+// C-ABI
+// ============================================================================
+extern "C" void db_default_opts(db_opts* o, db_gcv_opts* g) {
+  if (o) {
+    o->tol_fine = 1e-3; o->tol_coarse = 1e-6; o->kmax = 50;
+    o->eps_irls = 0.03; o->eps_mm = 0.03; o->tau_sb = 0.005;
+    o->lsqr_atol = 1e-6; o->lsqr_btol = 1e-6; o->lsqr_conlim = 1e8; o->lsqr_maxit = 100;
+    o->lsqr_warm_start = 1; o->precision = DB_PREC_FP32;
+  }
+  if (g) {
+    g->grid_points = 50; g->log10_gamma_lo = -10.0; g->log10_gamma_hi = 2.0;
+    g->refine_tol_log10 = 1e-5; g->gcv_estimates = 3; g->proj_dim = 40; g->proj_dim_max = 160;
+    g->gamma_fixed = 0.0;
+  }
+}
+
+extern "C" const char* db_last_error(db_context* ctx) { return ctx ? ctx->err.c_str() : g_last_error.c_str(); }
+
+extern "C" db_status db_context_create(db_context** out, int device, size_t budget) {
+  if (!out) return DB_EINVAL;
+  try {
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    REQUIRE(device >= 0 && device < ndev, "no such CUDA device");
+    CK(cudaSetDevice(device));
+    db_context* c = new db_context();
+    c->device = device;
+    c->arena.budget = budget;
+    CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device));
+    *out = c;
+    return DB_OK;
+  } catch (DbError& e) {
+    g_last_error = e.msg;
+    return e.st;
+  }
+}
+
+extern "C" db_status db_set_profiling(db_context* c, int on) {
+  if (!c) return DB_EINVAL;
+  try {
+    CK(cudaSetDevice(c->device));
+    if (on && !c->ev0) {
+      CK(cudaEventCreate(&c->ev0));
+      CK(cudaEventCreate(&c->ev1));
+    }
+    c->profiling = on ? 1 : 0;
+    return DB_OK;
+  } catch (DbError& e) {
+    c->err = e.msg;
+    return e.st;
+  }
+}
+
+extern "C" db_status db_get_stats(db_context* c, db_stats* out) {
+  if (!c || !out) return DB_EINVAL;
+  *out = c->stats;
+  return DB_OK;
+}
+
+extern "C" db_status db_reset_stats(db_context* c) {
+  if (!c) return DB_EINVAL;
+  c->stats = db_stats{};
+  return DB_OK;
+}
+
+extern "C" db_status db_context_destroy(db_context* c) {
+  if (!c) return DB_EINVAL;
+  cudaSetDevice(c->device);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->arena.base) cudaFree(c->arena.base);
+  delete c;
+  return DB_OK;
+}
+
+extern "C" size_t db_footprint_bytes(int m, int levels, int S, db_precision prec, const db_gcv_opts* gcv) {
+  db_gcv_opts g;
+  db_default_opts(nullptr, &g);
+  if (gcv) g = *gcv;
+  if (prec == DB_PREC_FP64) return Engine<double>::footprint(m, levels, S, g);
+  if (prec == DB_PREC_BF16) return Engine<__nv_bfloat16>::footprint(m, levels, S, g);
+  return Engine<float>::footprint(m, levels, S, g);
+}
+
+static void validate(int m, int S, int levels, db_wavelet wv) {
+  REQUIRE(m >= 2 && (m & (m - 1)) == 0, "m must be a power of two");
+  REQUIRE(S >= 1 && (S & 1) == 1 && S < m, "PSF size must be odd and smaller than m");
+  REQUIRE(wv == DB_HAAR || wv == DB_DB4, "unknown wavelet");
+  REQUIRE(levels >= 1 && levels <= 16, "levels out of range");
+  const int kappa = wv == DB_HAAR ? 2 : 4;
+  REQUIRE((m >> (levels - 1)) >= kappa && (m >> (levels - 1)) >= 2, "coarsest level smaller than the filter");
+}
+
+template <typename T>
+static void run_solve(db_context* ctx, cudaStream_t st, const double* b_dev, int m, const double* psf_dev, int S,
+                      db_solver solver, db_wavelet wv, int levels, db_transfer tr, const db_gcv_opts& g,
+                      const db_opts& o, double* x_dev, double* mu, int* iters, int* inner) {
+  Engine<T> E(ctx, st);
+  E.o = o;
+  E.go = g;
+  ctx->arena.ensure(Engine<T>::footprint(m, levels, S, g));
+  ctx->arena.reset();
+  E.build(psf_dev, S, m, levels, wv, b_dev, true);
+  E.vcycle(solver, wv, levels == 1 ? DB_APPROACH_I : tr, mu, iters, inner);
+  { count_launch(); k_convert_out<T><<<grid_for((size_t)m * m, ctx->nsm), 256, 0, st>>>((size_t)m * m, E.H.lv[0].xa, x_dev); }
+  CK(cudaGetLastError());
+}
+
+extern "C" db_status deblur_solve(db_context* ctx, const double* b, int m, const double* psf, int S, db_solver solver,
+                       db_wavelet wavelet, int levels, db_transfer transfer, const db_gcv_opts* gcv,
+                       const db_opts* opts, double* x, double* mu_per_level, int* iters_per_level,
+                       int* inner_iters_per_level, int on_device, db_stream stream) {
+  if (!ctx) return DB_EINVAL;
+  CountScope count_scope(ctx);
+  try {
+    REQUIRE(b && psf && x && mu_per_level && iters_per_level, "null pointer argument");
+    validate(m, S, levels, wavelet);
+    REQUIRE(solver >= DB_IRLS && solver <= DB_SB, "unknown solver");
+    REQUIRE(transfer >= DB_APPROACH_I && transfer <= DB_APPROACH_D, "unknown transfer strategy");
+    db_opts o;
+    db_gcv_opts g;
+    db_default_opts(&o, &g);
+    if (opts) o = *opts;
+    if (gcv) g = *gcv;
+    REQUIRE(g.proj_dim >= 1 && g.proj_dim_max >= g.proj_dim && g.grid_points >= 3, "bad GCV options");
+    REQUIRE(o.kmax >= 1 && o.lsqr_maxit >= 1, "bad iteration limits");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)m * m;
+    double *db_ = nullptr, *dpsf = nullptr, *dx = nullptr;
+    std::vector<double> hx;
+    if (!on_device) {
+      CK(cudaMallocAsync((void**)&db_, n * sizeof(double), st));
+      CK(cudaMallocAsync((void**)&dpsf, (size_t)S * S * sizeof(double), st));
+      CK(cudaMallocAsync((void**)&dx, n * sizeof(double), st));
+      CK(cudaMemcpyAsync(db_, b, n * sizeof(double), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(dpsf, psf, (size_t)S * S * sizeof(double), cudaMemcpyHostToDevice, st));
+    } else {
+      db_ = const_cast<double*>(b);
+      dpsf = const_cast<double*>(psf);
+      dx = x;
+    }
+    std::vector<double> mu(levels, 0.0);
+    std::vector<int> it(levels, 0), inn(levels, 0);
+    if (o.precision == DB_PREC_FP64)
+      run_solve<double>(ctx, st, db_, m, dpsf, S, solver, wavelet, levels, transfer, g, o, dx, mu.data(), it.data(), inn.data());
+    else if (o.precision == DB_PREC_BF16)
+      run_solve<__nv_bfloat16>(ctx, st, db_, m, dpsf, S, solver, wavelet, levels, transfer, g, o, dx, mu.data(), it.data(), inn.data());
+    else
+      run_solve<float>(ctx, st, db_, m, dpsf, S, solver, wavelet, levels, transfer, g, o, dx, mu.data(), it.data(), inn.data());
+    if (!on_device) {
+      CK(cudaMemcpyAsync(x, dx, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaFreeAsync(db_, st));
+      CK(cudaFreeAsync(dpsf, st));
+      CK(cudaFreeAsync(dx, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < levels; ++i) {
+      mu_per_level[i] = mu[i];
+      iters_per_level[i] = it[i];
+      if (inner_iters_per_level) inner_iters_per_level[i] = inn[i];
+    }
+    return DB_OK;
+  } catch (DbError& e) {
+    ctx->err = e.msg;
+    return e.st;
+  }
+}
+
+// ---- operator-level entry points ---------------------------------------------
+template <typename T>
+static void op_blur(db_context* ctx, cudaStream_t st, const double* psf_host, int S, int m, db_wavelet wv, int level,
+                    int tr, const void* x, void* y) {
+  Engine<T> E(ctx, st);
+  db_default_opts(&E.o, &E.go);
+  ctx->arena.ensure(Engine<T>::footprint(m, level + 1, S, E.go));
+  ctx->arena.reset();
+  double* dpsf = ctx->arena.take<double>((size_t)S * S);
+  CK(cudaMemcpyAsync(dpsf, psf_host, (size_t)S * S * sizeof(double), cudaMemcpyHostToDevice, st));
+  E.build(dpsf, S, m, level + 1, wv, nullptr, false);
+  E.blur_T(E.H.lv[level], tr != 0, (const T*)x, (T*)y);
+}
+
+extern "C" db_status db_apply_blur(db_context* ctx, const double* psf_host, int S, int m, db_wavelet wv, int level, int tr,
+                        const void* x, void* y, db_precision prec, db_stream stream) {
+  if (!ctx) return DB_EINVAL;
+  CountScope count_scope(ctx);
+  try {
+    REQUIRE(psf_host && x && y, "null pointer argument");
+    validate(m, S, level + 1, wv);
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == DB_PREC_FP64) op_blur<double>(ctx, st, psf_host, S, m, wv, level, tr, x, y);
+    else if (prec == DB_PREC_FP32) op_blur<float>(ctx, st, psf_host, S, m, wv, level, tr, x, y);
+    else REQUIRE(false, "operator entry points take FP64 or FP32 buffers");
+    CK(cudaStreamSynchronize(st));
+    return DB_OK;
+  } catch (DbError& e) {
+    ctx->err = e.msg;
+    return e.st;
+  }
+}
+
+template <typename F>
+static db_status simple_call(F&& f) {
+  try {
+    f();
+    return DB_OK;
+  } catch (DbError& e) {
+    g_last_error = e.msg;
+    return e.st;
+  }
+}
+
+static int dev_sms() {
+  int d = 0, n = 0;
+  cudaGetDevice(&d);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
+  return n > 0 ? n : 1;
+}
+
+extern "C" db_status db_apply_L(int m, const void* x, void* q, db_precision prec, db_stream stream) {
+  return simple_call([&] {
+    REQUIRE(m >= 2 && x && q, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t n = (size_t)m * m;
+    int g = grid_for(n, dev_sms());
+    if (prec == DB_PREC_FP64) { count_launch(); k_L<double><<<g, 256, 0, st>>>(m, (const double*)x, (double*)q, (double*)q + n); }
+    else if (prec == DB_PREC_FP32) { count_launch(); k_L<float><<<g, 256, 0, st>>>(m, (const float*)x, (float*)q, (float*)q + n); }
+    else REQUIRE(false, "FP64 or FP32 only");
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+  });
+}
+
+extern "C" db_status db_apply_Lt(int m, const void* q, void* x, db_precision prec, db_stream stream) {
+  return simple_call([&] {
+    REQUIRE(m >= 2 && x && q, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t n = (size_t)m * m;
+    int g = grid_for(n, dev_sms());
+    if (prec == DB_PREC_FP64) { count_launch(); k_Lt<double><<<g, 256, 0, st>>>(m, (const double*)q, (const double*)q + n, (double*)x); }
+    else if (prec == DB_PREC_FP32) { count_launch(); k_Lt<float><<<g, 256, 0, st>>>(m, (const float*)q, (const float*)q + n, (float*)x); }
+    else REQUIRE(false, "FP64 or FP32 only");
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+  });
+}
+
+extern "C" db_status db_restrict(int m, db_wavelet wv, const void* x, void* y, db_precision prec, db_stream stream) {
+  return simple_call([&] {
+    REQUIRE(m >= 4 && (m & 1) == 0 && x && y, "bad arguments");
+    REQUIRE(wv == DB_HAAR || wv == DB_DB4, "unknown wavelet");
+    REQUIRE(m >= make_filter(wv).kappa, "m smaller than the filter");
+    cudaStream_t st = (cudaStream_t)stream;
+    int g = grid_for((size_t)m * m / 4, dev_sms());
+    if (prec == DB_PREC_FP64) { count_launch(); k_restrict<double><<<g, 256, 0, st>>>(m, make_filter(wv), (const double*)x, (double*)y); }
+    else if (prec == DB_PREC_FP32) { count_launch(); k_restrict<float><<<g, 256, 0, st>>>(m, make_filter(wv), (const float*)x, (float*)y); }
+    else REQUIRE(false, "FP64 or FP32 only");
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+  });
+}
+
+extern "C" db_status db_prolong(int mc, db_wavelet wv, const void* y, void* x, db_precision prec, db_stream stream) {
+  return simple_call([&] {
+    REQUIRE(mc >= 1 && x && y, "bad arguments");
+    REQUIRE(wv == DB_HAAR || wv == DB_DB4, "unknown wavelet");
+    REQUIRE(2 * mc >= make_filter(wv).kappa, "m smaller than the filter");
+    cudaStream_t st = (cudaStream_t)stream;
+    int g = grid_for((size_t)mc * mc * 4, dev_sms());
+    if (prec == DB_PREC_FP64) { count_launch(); k_prolong<double><<<g, 256, 0, st>>>(mc, make_filter(wv), (const double*)y, (double*)x, 0, 0); }
+    else if (prec == DB_PREC_FP32) { count_launch(); k_prolong<float><<<g, 256, 0, st>>>(mc, make_filter(wv), (const float*)y, (float*)x, 0, 0); }
+    else REQUIRE(false, "FP64 or FP32 only");
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+  });
+}
+
+extern "C" db_status db_aux_prolong(int mc, db_wavelet wv, const void* qc, void* qf, db_precision prec, db_stream stream) {
+  return simple_call([&] {
+    REQUIRE(mc >= 1 && qc && qf, "bad arguments");
+    REQUIRE(wv == DB_HAAR || wv == DB_DB4, "unknown wavelet");
+    REQUIRE(2 * mc >= make_filter(wv).kappa, "m smaller than the filter");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nc = (size_t)mc * mc, nf = nc * 4;
+    int g = grid_for(nf, dev_sms());
+    Filter f = make_filter(wv);
+    if (prec == DB_PREC_FP64) {
+      { count_launch(); k_prolong<double><<<g, 256, 0, st>>>(mc, f, (const double*)qc, (double*)qf, 1, 0); }
+      { count_launch(); k_prolong<double><<<g, 256, 0, st>>>(mc, f, (const double*)qc + nc, (double*)qf + nf, 0, 1); }
+    } else if (prec == DB_PREC_FP32) {
+      { count_launch(); k_prolong<float><<<g, 256, 0, st>>>(mc, f, (const float*)qc, (float*)qf, 1, 0); }
+      { count_launch(); k_prolong<float><<<g, 256, 0, st>>>(mc, f, (const float*)qc + nc, (float*)qf + nf, 0, 1); }
+    } else REQUIRE(false, "FP64 or FP32 only");
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+  });
+}
+
+template <typename T>
+static void op_lsqr(db_context* ctx, cudaStream_t st, const double* psf_host, int S, int m, db_solver solver,
+                    double gamma, const void* b, const void* x0, const void* aux0, const void* aux1, void* x_out,
+                    const db_opts& o, int* iters) {
+  Engine<T> E(ctx, st);
+  db_default_opts(nullptr, &E.go);
+  E.o = o;
+  ctx->arena.ensure(Engine<T>::footprint(m, 1, S, E.go));
+  ctx->arena.reset();
+  double* dpsf = ctx->arena.take<double>((size_t)S * S);
+  CK(cudaMemcpyAsync(dpsf, psf_host, (size_t)S * S * sizeof(double), cudaMemcpyHostToDevice, st));
+  E.build(dpsf, S, m, 1, DB_HAAR, nullptr, true);
+  Level<T>& L = E.H.lv[0];
+  const size_t n = L.n;
+  CK(cudaMemcpyAsync(L.b, b, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  const T* a0 = (const T*)aux0;
+  const T* a1 = (const T*)aux1;
+  if (a0) {
+    CK(cudaMemcpyAsync(L.a0x, a0, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(L.a0y, a0 + n, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  } else {
+    { count_launch(); k_fill<T><<<grid_for(n, ctx->nsm), 256, 0, st>>>(n, L.a0x, solver == DB_IRLS ? 1.0 : 0.0); }
+    { count_launch(); k_fill<T><<<grid_for(n, ctx->nsm), 256, 0, st>>>(n, L.a0y, solver == DB_IRLS ? 1.0 : 0.0); }
+  }
+  if (a1) {
+    CK(cudaMemcpyAsync(L.a1x, a1, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(L.a1y, a1 + n, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  } else {
+    { count_launch(); k_fill<T><<<grid_for(n, ctx->nsm), 256, 0, st>>>(n, L.a1x, 0.0); }
+    { count_launch(); k_fill<T><<<grid_for(n, ctx->nsm), 256, 0, st>>>(n, L.a1y, 0.0); }
+  }
+  if (x0) CK(cudaMemcpyAsync(L.xa, x0, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  else { count_launch(); k_fill<T><<<grid_for(n, ctx->nsm), 256, 0, st>>>(n, L.xa, 0.0); }
+  *iters = E.lsqr(L, solver, gamma, o.lsqr_warm_start ? L.xa : nullptr);
+  // x_out = x0 + delta (no auxiliary update: copy, then add)
+  const int g = grid_for(n, ctx->nsm);
+  { count_launch(); k_outer_update<T><<<g, 256, 0, st>>>(m, -1, o.lsqr_warm_start, L.xa, L.dlt, (T*)x_out, L.a0x, L.a0y, L.a1x,
+                                       L.a1y, 0, 0, 0, E.d_part, E.d_cnt + 4, E.d_box); }
+  CK(cudaGetLastError());
+}
+
+extern "C" db_status db_lsqr_solve(db_context* ctx, const double* psf_host, int S, int m, db_solver solver, double gamma,
+                        const void* b, const void* x0, const void* aux0, const void* aux1, void* x_out,
+                        const db_opts* opts, int* iters, db_precision prec, db_stream stream) {
+  if (!ctx) return DB_EINVAL;
+  CountScope count_scope(ctx);
+  try {
+    REQUIRE(psf_host && b && x_out && iters, "null pointer argument");
+    validate(m, S, 1, DB_HAAR);
+    REQUIRE(gamma > 0, "gamma must be positive");
+    db_opts o;
+    db_default_opts(&o, nullptr);
+    if (opts) o = *opts;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == DB_PREC_FP64) op_lsqr<double>(ctx, st, psf_host, S, m, solver, gamma, b, x0, aux0, aux1, x_out, o, iters);
+    else if (prec == DB_PREC_FP32) op_lsqr<float>(ctx, st, psf_host, S, m, solver, gamma, b, x0, aux0, aux1, x_out, o, iters);
+    else REQUIRE(false, "FP64 or FP32 only");
+    CK(cudaStreamSynchronize(st));
+    return DB_OK;
+  } catch (DbError& e) {
+    ctx->err = e.msg;
+    return e.st;
+  }
+}
+
+template <typename T>
+static void op_gcv(db_context* ctx, cudaStream_t st, const double* psf_host, int S, int m, db_solver solver,
+                   const void* b, const void* aux0, const void* aux1, const db_gcv_opts& g, double* gamma_out) {
+  Engine<T> E(ctx, st);
+  db_default_opts(&E.o, nullptr);
+  E.go = g;
+  ctx->arena.ensure(Engine<T>::footprint(m, 1, S, g));
+  ctx->arena.reset();
+  double* dpsf = ctx->arena.take<double>((size_t)S * S);
+  CK(cudaMemcpyAsync(dpsf, psf_host, (size_t)S * S * sizeof(double), cudaMemcpyHostToDevice, st));
+  E.build(dpsf, S, m, 1, DB_HAAR, nullptr, true);
+  Level<T>& L = E.H.lv[0];
+  const size_t n = L.n;
+  CK(cudaMemcpyAsync(L.b, b, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  const T* a0 = (const T*)aux0;
+  const T* a1 = (const T*)aux1;
+  if (a0) {
+    CK(cudaMemcpyAsync(L.a0x, a0, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(L.a0y, a0 + n, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  }
+  if (a1) {
+    CK(cudaMemcpyAsync(L.a1x, a1, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(L.a1y, a1 + n, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  } else {
+    { count_launch(); k_fill<T><<<grid_for(n, ctx->nsm), 256, 0, st>>>(n, L.a1x, 0.0); }
+    { count_launch(); k_fill<T><<<grid_for(n, ctx->nsm), 256, 0, st>>>(n, L.a1y, 0.0); }
+  }
+  const bool weighted = (solver == DB_IRLS) && a0;
+  const bool shifted = (solver != DB_IRLS) && a0;
+  *gamma_out = E.gcv(L, solver, weighted, shifted);
+}
+
+extern "C" db_status db_gcv_select(db_context* ctx, const double* psf_host, int S, int m, db_solver solver, const void* b,
+                        const void* aux0, const void* aux1, const db_gcv_opts* gcv, double* gamma_out,
+                        db_precision prec, db_stream stream) {
+  if (!ctx) return DB_EINVAL;
+  CountScope count_scope(ctx);
+  try {
+    REQUIRE(psf_host && b && gamma_out, "null pointer argument");
+    validate(m, S, 1, DB_HAAR);
+    db_gcv_opts g;
+    db_default_opts(nullptr, &g);
+    if (gcv) g = *gcv;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == DB_PREC_FP64) op_gcv<double>(ctx, st, psf_host, S, m, solver, b, aux0, aux1, g, gamma_out);
+    else if (prec == DB_PREC_FP32) op_gcv<float>(ctx, st, psf_host, S, m, solver, b, aux0, aux1, g, gamma_out);
+    else REQUIRE(false, "FP64 or FP32 only");
+    CK(cudaStreamSynchronize(st));
+    return DB_OK;
+  } catch (DbError& e) {
+    ctx->err = e.msg;
+    return e.st;
+  }
+}
+

@@ -1,0 +1,53 @@
+"""GPU GCV selection (projected form, Sec. 3) against the oracle's."""
+import numpy as np
+import pytest
+
+from oracle import operators as O
+from oracle import solvers as S
+from paper_2608_17123_b300 import api
+from paper_2608_17123_b300 import inputs as I
+
+from helpers import img_to_dev, planes_to_dev
+from perturb import noisy
+
+pytestmark = pytest.mark.gpu
+
+
+def problem(m, sigma=2.0, Sz=9, seed=0):
+    x_true = I.phantom(m, 12, 6, seed)
+    g = I.gaussian_factor(sigma, Sz)
+    A = O.KronOp.from_factors(m, g, g)
+    b = I.add_noise(A.apply(x_true), I.noise_direction(m, 100 + seed), 0.01)
+    return A, b, x_true, np.outer(g, g)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind", ["plain", "irls", "mm", "sb"])
+@pytest.mark.parametrize("m", [32, 64])
+def test_gcv_matches_oracle(prec, kind, m):
+    import torch
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    A, b, x_true, psf = problem(m)
+    x0 = 0.8 * x_true + 0.02
+    qx, qy = O.L_apply(x0)
+    a0 = a1 = None
+    if kind == "irls":
+        a0 = S.irls_weights(qx, qy, 0.03)
+        sub = S.Subproblem(A, b, weights=a0)
+    elif kind == "mm":
+        a0 = S.mm_surrogate(qx, qy, 0.03)
+        sub = S.Subproblem(A, b, c=a0)
+    elif kind == "sb":
+        a0 = (S.shrink(qx, 0.005), S.shrink(qy, 0.005))
+        a1 = (0.5 * (qx - a0[0]), 0.5 * (qy - a0[1]))
+        sub = S.Subproblem(A, b, c=(a0[0] - a1[0], a0[1] - a1[1]))
+    else:
+        sub = S.Subproblem(A, b)
+    g_ref = sub.gcv(S.opts_with())
+    g_sp = noisy(lambda: sub.gcv(S.opts_with()), prec)
+    spread = abs(g_sp - g_ref) / g_ref
+    solver = {"plain": "mm", "irls": "irls", "mm": "mm", "sb": "sb"}[kind]
+    g = api.gcv_select(psf, m, solver, img_to_dev(b, dt),
+                       None if a0 is None else planes_to_dev(*a0, dt),
+                       None if a1 is None else planes_to_dev(*a1, dt))
+    assert abs(g - g_ref) <= max(1e-2, 10 * spread) * g_ref, (g, g_ref, g_sp)

@@ -1,0 +1,84 @@
+"""GPU LSQR (persistent cooperative kernel) against the oracle's LSQR on the
+augmented problem of Eq. (augmented), for the IRLS, MM and SB forms."""
+import numpy as np
+import pytest
+
+from oracle import operators as O
+from oracle import solvers as S
+from paper_2608_17123_b300 import api
+from paper_2608_17123_b300 import inputs as I
+
+from helpers import dev_to_img, img_to_dev, planes_to_dev, rel
+from perturb import noisy
+
+pytestmark = pytest.mark.gpu
+RNG = np.random.default_rng(11)
+
+
+def problem(m, sigma=2.0, Sz=9, seed=0):
+    x_true = I.phantom(m, 12, 6, seed)
+    g = I.gaussian_factor(sigma, Sz)
+    A = O.KronOp.from_factors(m, g, g)
+    b = I.add_noise(A.apply(x_true), I.noise_direction(m, 100 + seed), 0.01)
+    return A, b, x_true, np.outer(g, g)
+
+
+def aux_for(solver, x, m):
+    qx, qy = O.L_apply(x)
+    if solver == "irls":
+        return S.irls_weights(qx, qy, 0.03), None
+    if solver == "mm":
+        return S.mm_surrogate(qx, qy, 0.03), None
+    d = (S.shrink(qx, 0.005), S.shrink(qy, 0.005))
+    g = (qx - d[0] + 0.001 * RNG.standard_normal(qx.shape), qy - d[1])
+    return d, g
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("solver", ["irls", "mm", "sb"])
+@pytest.mark.parametrize("m", [16, 64, 128])
+def test_lsqr_matches_oracle(prec, solver, m):
+    import torch
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    A, b, x_true, psf = problem(m)
+    x0 = 0.9 * x_true
+    a0, a1 = aux_for(solver, x0, m)
+    gamma = 2e-4
+    o = S.opts_with()
+    sub = S.Subproblem(A, b, weights=a0 if solver == "irls" else None,
+                       c=None if solver == "irls" else (a0 if solver == "mm" else (a0[0] - a1[0], a0[1] - a1[1])))
+    x_ref, its_ref = sub.solve(gamma, x0, o)
+    x_sp, its_sp = noisy(lambda: sub.solve(gamma, x0, o), prec)
+    spread, spread_it = rel(x_sp, x_ref), abs(its_sp - its_ref)
+    xo = torch.empty(m * m, device="cuda", dtype=dt)
+    its = api.lsqr_solve(psf, m, solver, gamma, img_to_dev(b, dt), img_to_dev(x0, dt),
+                         planes_to_dev(*a0, dt), None if a1 is None else planes_to_dev(*a1, dt), xo)
+    x = dev_to_img(xo, m)
+    target = 1e-10 if prec == "fp64" else 1e-5
+    assert abs(its - its_ref) <= max(1, 2 * spread_it), (its, its_ref, its_sp)
+    assert rel(x, x_ref) <= max(target, 10 * spread), (rel(x, x_ref), spread)
+
+
+def test_lsqr_cold_start_and_tiny():
+    import torch
+    m = 8
+    A, b, _, psf = problem(m, 1.0, 5)
+    o = S.opts_with(lsqr_warm_start=False)
+    x_ref, its_ref = S.Subproblem(A, b).solve(1e-3, np.zeros((m, m)), o)
+    xo = torch.empty(m * m, device="cuda", dtype=torch.float64)
+    ones = (np.ones((m - 1, m)), np.ones((m, m - 1)))
+    its = api.lsqr_solve(psf, m, "irls", 1e-3, img_to_dev(b, torch.float64), None,
+                         planes_to_dev(*ones, torch.float64), None, xo, lsqr_warm_start=0)
+    x_sp, _ = noisy(lambda: S.Subproblem(A, b).solve(1e-3, np.zeros((m, m)), o), "fp64")
+    assert abs(its - its_ref) <= 1
+    assert rel(dev_to_img(xo, m), x_ref) <= max(1e-10, 10 * rel(x_sp, x_ref))
+
+
+def test_lsqr_zero_rhs():
+    import torch
+    m = 32
+    _, _, _, psf = problem(m)
+    z = torch.zeros(m * m, device="cuda", dtype=torch.float32)
+    xo = torch.full((m * m,), 5.0, device="cuda", dtype=torch.float32)
+    its = api.lsqr_solve(psf, m, "mm", 1e-3, z, z, torch.zeros(2 * m * m, device="cuda"), None, xo)
+    assert its == 0 and float(xo.abs().max()) == 0.0

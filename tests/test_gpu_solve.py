@@ -1,0 +1,95 @@
+"""End-to-end V-cycle solves (Alg. 4 with Alg. 1-3) on the GPU against the
+FP64 oracle: reconstruction, per-level outer iteration counts and gamma.
+
+The method is sensitive to rounding-level perturbations (LSQR without
+reorthogonalisation stopped at its iteration limit, GCV on small coarse
+levels), so the oracle rerun with unit-roundoff noise of the storage
+precision injected into every operator output (tests/perturb.py) already
+differs from the plain oracle run. Each tolerance is the larger of the
+stated target (x: 1e-4 FP32, 1e-6 FP64; gamma: 1 %; outer iterations: +-1)
+and ten times that measured spread.
+"""
+import numpy as np
+import pytest
+
+from oracle import operators as O
+from oracle import solvers as S
+from paper_2608_17123_b300 import api
+from paper_2608_17123_b300 import inputs as I
+
+from helpers import rel
+from perturb import noisy
+
+pytestmark = pytest.mark.gpu
+
+_CACHE = {}
+XTOL = {"fp64": 1e-6, "fp32": 1e-4}
+
+
+def case(m, sigma, Sz, nr, nd, seed, noise):
+    key = (m, sigma, Sz, nr, nd, seed, noise)
+    if key not in _CACHE:
+        x_true = I.phantom(m, nr, nd, seed)
+        g = I.gaussian_factor(sigma, Sz)
+        A = O.KronOp.from_factors(m, g, g)
+        b = I.add_noise(A.apply(x_true), I.noise_direction(m, 100 + seed), noise)
+        _CACHE[key] = (A, b, x_true, np.outer(g, g))
+    return _CACHE[key]
+
+
+def references(A, b, combo, prec):
+    key = ("ref", id(A), combo, prec)
+    if key not in _CACHE:
+        r0 = S.mgm(b, A, *combo)
+        r1 = noisy(lambda: S.mgm(b, A, *combo), prec)
+        _CACHE[key] = (r0, r1)
+    return _CACHE[key]
+
+
+def compare(r, r0, r1, prec):
+    spread_x = rel(r1["x"], r0["x"])
+    d = rel(r["x"], r0["x"])
+    assert d <= max(XTOL[prec], 10 * spread_x), f"x rel diff {d:.2e} (oracle spread {spread_x:.2e})"
+    for i in range(len(r0["iters"])):
+        spread_it = abs(r1["iters"][i] - r0["iters"][i])
+        assert abs(r["iters"][i] - r0["iters"][i]) <= max(1, 2 * spread_it), (i, r["iters"], r0["iters"], r1["iters"])
+        spread_mu = abs(r1["mu"][i] - r0["mu"][i]) / r0["mu"][i]
+        dm = abs(r["mu"][i] - r0["mu"][i]) / r0["mu"][i]
+        assert dm <= max(1e-2, 10 * spread_mu), (i, r["mu"], r0["mu"], r1["mu"])
+    return d, spread_x
+
+
+COMBOS = [("irls", "haar", 1, "X"), ("irls", "haar", 2, "X"), ("irls", "db4", 3, "D"),
+          ("mm", "haar", 2, "D"), ("mm", "db4", 3, "X"), ("mm", "haar", 1, "X"),
+          ("sb", "db4", 2, "X"), ("sb", "haar", 3, "D"), ("sb", "db4", 1, "X")]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("combo", COMBOS, ids=["-".join(map(str, c)) for c in COMBOS])
+def test_solve_matches_oracle_m32(prec, combo):
+    A, b, _, psf = case(32, 1.5, 7, 6, 3, 1, 0.01)
+    r0, r1 = references(A, b, combo, prec)
+    r = api.deblur_solve(b, psf, *combo, precision=prec)
+    compare(r, r0, r1, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_solve_config_m64_irls(prec):
+    """m = 64, sigma = 2 on 9 x 9, 1 % noise, IRLS in a 2-level Haar cycle
+    transferring the solution."""
+    A, b, x_true, psf = case(64, 2.0, 9, 12, 6, 0, 0.01)
+    r0, r1 = references(A, b, ("irls", "haar", 2, "X"), prec)
+    r = api.deblur_solve(b, psf, "irls", "haar", 2, "X", precision=prec)
+    compare(r, r0, r1, prec)
+    assert rel(r["x"], x_true) < 0.3
+
+
+def test_solve_rejects_bad_arguments():
+    from paper_2608_17123_b300._lib import DeblurError
+    b = np.zeros((48, 48))
+    with pytest.raises(DeblurError):
+        api.deblur_solve(b, np.ones((3, 3)) / 9)          # m not a power of two
+    with pytest.raises(DeblurError):
+        api.deblur_solve(np.zeros((16, 16)), np.ones((4, 4)) / 16)   # even PSF
+    with pytest.raises(DeblurError):
+        api.deblur_solve(np.zeros((16, 16)), np.ones((3, 3)) / 9, "mm", "db4", 4, "X")  # coarsest 2 < 4 taps
