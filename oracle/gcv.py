@@ -43,33 +43,40 @@ class GcvFactors:
     """The small diagonal form of the GCV functional.
 
     With a basis Y such that Y^T G_A Y = diag(lam), Y^T (G_A + G_D) Y = I,
-    a = Y^T g_A, d = Y^T g_D and ahat_j = a_j / sqrt(lam_j), the data residual
-    of x_gamma is a sum of squares (no cancellation between gamma-dependent
-    terms):
+    a = Y^T g_A and d = Y^T g_D, the trial solution in the eigenbasis is
+    z_j = (a_j + gamma d_j) / (lam_j + gamma (1 - lam_j)), and the data residual
+    splits into a gamma-dependent quadratic form and a constant without any
+    cancellation between gamma-dependent terms:
 
-      ||A x_gamma - b||^2 = sum_j [gamma (sqrt(lam_j) d_j - ahat_j (1 - lam_j))
-                                   / (lam_j + gamma (1 - lam_j))]^2 + r0^2,
-      r0^2 = ||b||^2 - sum_j ahat_j^2   (residual of b outside range(A V)).
+      w0_j = a_j / (lam_j + eta),   f_j = a_j + d_j - w0_j,
+      ||A x_gamma - b||^2 = gamma^2 sum_j lam_j (f_j / (lam_j + gamma (1 - lam_j)))^2 + r0^2,
+      r0^2 = ||b||^2 - sum_j a_j w0_j   (b outside the resolved range of A V).
+
+    With eta = 0 (the default, used everywhere) this is exact algebra (w0 is
+    the gamma -> 0 solution); eta > 0 would count pencil directions with
+    lam_j << eta as outside range(A). Note that forming A^T A squares the
+    conditioning: on a level where A is numerically singular (pencil
+    eigenvalues ~ 1e-16) the numerator of any Gram-matrix formulation carries
+    errors of order 1e-2 against a QR-based least-squares residual.
 
     ``trace`` is a callable gamma -> tr(A A_gamma^# ); by default the exact
     sum_j lam_j / (lam_j + gamma (1 - lam_j)).
     """
 
-    def __init__(self, lam, a, d, bnorm2, n, trace=None):
+    def __init__(self, lam, a, d, bnorm2, n, trace=None, eta=0.0):
         self.lam = np.asarray(lam, dtype=np.float64)
         self.a = np.asarray(a, dtype=np.float64)
         self.d = np.asarray(d, dtype=np.float64)
         self.n = n
-        pos = self.lam > 0.0
-        self.ahat = np.where(pos, self.a / np.sqrt(np.where(pos, self.lam, 1.0)), 0.0)
-        self.r02 = max(float(bnorm2) - float(np.sum(self.ahat ** 2)), 0.0)
-        self.sl = np.sqrt(np.maximum(self.lam, 0.0))
+        den = self.lam + eta
+        self.w0 = np.where(den > 0.0, self.a / np.where(den > 0.0, den, 1.0), 0.0)
+        self.f = self.a + self.d - self.w0
+        self.r02 = max(float(bnorm2) - float(np.sum(self.a * self.w0)), 0.0)
         self._trace = trace
 
     def numerator(self, gamma: float) -> float:
-        den = self.lam + gamma * (1.0 - self.lam)
-        e = gamma * (self.sl * self.d - self.ahat * (1.0 - self.lam)) / den
-        return float(np.sum(e * e)) + self.r02
+        u = self.f / (self.lam + gamma * (1.0 - self.lam))
+        return gamma * gamma * float(np.sum(self.lam * u * u)) + self.r02
 
     def trace(self, gamma: float) -> float:
         if self._trace is not None:
@@ -80,10 +87,13 @@ class GcvFactors:
         return self.numerator(gamma) / (self.n - self.trace(gamma)) ** 2
 
 
-def reduce_pair(GA, GD, gA, gD, bnorm2, n, trace=None) -> GcvFactors:
+EXACT_RANK_ETA = 0.0
+
+
+def reduce_pair(GA, GD, gA, gD, bnorm2, n, trace=None, eta=0.0) -> GcvFactors:
     """Generalized symmetric eigenproblem GA y = lam (GA + GD) y."""
     lam, Y = sla.eigh(GA, GA + GD)
-    return GcvFactors(lam, Y.T @ gA, Y.T @ gD, bnorm2, n, trace)
+    return GcvFactors(lam, Y.T @ gA, Y.T @ gD, bnorm2, n, trace, eta)
 
 
 def factors_exact(Ad, Dd, b, c, n) -> GcvFactors:
@@ -91,7 +101,7 @@ def factors_exact(Ad, Dd, b, c, n) -> GcvFactors:
     GA = Ad.T @ Ad
     GD = Dd.T @ Dd
     gD = Dd.T @ c if c is not None else np.zeros(Ad.shape[1])
-    return reduce_pair(GA, GD, Ad.T @ b, gD, float(b @ b), n)
+    return reduce_pair(GA, GD, Ad.T @ b, gD, float(b @ b), n, eta=EXACT_RANK_ETA)
 
 
 def _orth(x, basis):

@@ -5,6 +5,9 @@ Readings of points the paper leaves open (each is a default option here):
   * K_max = 50 outer iterations per level; RC = +inf when ||x^(k)|| = 0.
   * LSQR: atol = btol = 1e-6, conlim = 1e8, at most 100 iterations, warm
     started from x^(k) (it solves for the correction).
+  * GCV mode: exact (the paper's definition) on levels with at most 256
+    pixels, projected (see oracle.gcv) above; the projected Krylov basis on a
+    level of a few dozen pixels is dominated by rounding noise.
   * GCV schedule: MM and SB estimate gamma at outer iterations k = 0, 1, 2
     and keep the last value; IRLS re-estimates at every outer iteration,
     except on the finest level of a cycle with three or more levels, where
@@ -34,7 +37,7 @@ DEFAULTS = dict(
     eps_irls=0.03, eps_mm=0.03, tau_sb=0.005,
     lsqr_atol=1e-6, lsqr_btol=1e-6, lsqr_conlim=1e8, lsqr_maxit=100,
     lsqr_warm_start=True,
-    gcv_mode="projected", gcv_grid=50, gcv_lo=-10.0, gcv_hi=2.0, gcv_tolx=1e-5,
+    gcv_mode="auto", gcv_exact_max_n=256, gcv_grid=50, gcv_lo=-10.0, gcv_hi=2.0, gcv_tolx=1e-5,
     gcv_estimates=3, proj_dim=40, proj_dim_max=160,
     gamma_fixed=None,
 )
@@ -114,7 +117,10 @@ class Subproblem:
         if o.get("gamma_fixed") is not None:
             return float(o["gamma_fixed"])
         bv = O.vec(self.b)
-        if o["gcv_mode"] == "exact":
+        mode = o["gcv_mode"]
+        if mode == "auto":
+            mode = "exact" if self.n <= o["gcv_exact_max_n"] else "projected"
+        if mode == "exact":
             Ad = self.A.dense()
             Dd = O.L_dense(self.m)
             if self.wv is not None:
