@@ -51,8 +51,9 @@ typedef enum {
 } db_status;
 
 /* GCV options (Sec. 3). The paper evaluates the exact GCV functional through
- * the GSVD of the pair; this library uses the projected form: the numerator
- * is projected onto span{K_k(A^T A, A^T b), D^T c} and the trace term is
+ * the GSVD of the pair. This library does that on small levels (dense pair,
+ * exact trace) and otherwise uses a projected form: the numerator is
+ * projected onto span{K_k(A^T A, A^T b), D^T c} and the trace term is
  * evaluated for the same pair under periodic boundary conditions, where it
  * has a closed form. k starts at proj_dim and doubles while gamma moves by
  * more than 0.1 %, up to proj_dim_max. */
@@ -66,6 +67,8 @@ typedef struct {
   int    proj_dim;           /* 40                                            */
   int    proj_dim_max;       /* 160                                           */
   double gamma_fixed;        /* > 0: skip GCV and use this gamma everywhere   */
+  int    exact_max_pixels;   /* 256: levels with at most this many pixels use */
+                             /*   the exact GCV (dense pair, exact trace)     */
 } db_gcv_opts;
 
 typedef struct {
@@ -114,6 +117,70 @@ db_status deblur_solve(db_context* ctx, const double* b, int m, const double* ps
                        double* x, double* mu_per_level, int* iters_per_level,
                        int* inner_iters_per_level, int inputs_on_device, db_stream stream);
 
+/* ---- batched solves (an addition of this library, not in the paper) --------
+ * `count` independent solves advanced together: at every scheduler step each
+ * unfinished problem runs one outer iteration of its current level; all of
+ * their LSQR solves share one persistent cooperative launch (problems of any
+ * size, level and solver in one tile list), and their GCV evaluations run
+ * concurrently on a few internal streams. Results equal those of separate
+ * deblur_solve calls (same kernels, same per-problem arithmetic).
+ * Per request: b, psf, x as in deblur_solve (residence per
+ * `inputs_on_device`); mu/iters/inner outputs are host arrays of `levels`
+ * entries (inner may be NULL). All requests share `gcv` and `opts`
+ * (precision included). Synchronises `stream`. */
+typedef struct {
+  const double* b;
+  int m;
+  const double* psf;
+  int psf_size;
+  db_solver solver;
+  db_wavelet wavelet;
+  int levels;
+  db_transfer transfer;
+  double* x;
+  double* mu_per_level;
+  int* iters_per_level;
+  int* inner_iters_per_level;
+} db_request;
+
+db_status deblur_solve_batch(db_context* ctx, int count, const db_request* reqs, const db_gcv_opts* gcv,
+                             const db_opts* opts, int inputs_on_device, db_stream stream);
+
+/* ---- serving loop (an addition of this library, not in the paper) ---------
+ * Continuous batching of deblur solves: a scheduler thread keeps up to
+ * `max_resident` solves resident on the device (each with its own device
+ * arena holding its V-cycle state) and advances all of them one outer
+ * iteration per step, exactly as deblur_solve_batch does; a submitted request
+ * is admitted at the next step boundary once a slot is free and its device
+ * footprint (db_footprint_bytes without the shared GCV workspace) fits the
+ * budget. Results are identical to a separate deblur_solve of the same
+ * request (same kernels and per-problem arithmetic).
+ * Requests use host buffers: submit copies b and psf; x, mu, iters (and
+ * inner if not NULL) are written into the request's host buffers before the
+ * request is reported done; they must stay valid until then. FP32 storage.
+ * The server's scheduler thread uses the context: make no other call on the
+ * same context while a server created on it is alive (use a second context). */
+typedef struct db_server db_server;
+
+typedef struct {
+  int    max_resident;       /* solves advanced together (slots), >= 1       */
+  int    max_m;              /* largest image side that will be submitted    */
+  size_t hbm_budget_bytes;   /* device bytes for resident solves (0 = none)  */
+  db_opts opts;
+  db_gcv_opts gcv;
+} db_server_opts;
+
+db_status db_server_create(db_context* ctx, const db_server_opts* opts, db_server** out);
+/* Queue a request; returns at once with a ticket. DB_EINVAL for invalid
+ * requests (checked here), DB_EBUSY if the server is shutting down. */
+db_status db_server_submit(db_server* srv, const db_request* req, uint64_t* ticket);
+/* Wait up to timeout_us (< 0: forever) for a ticket: DB_OK when done (its
+ * outputs are written; latency_ms = submit to completion), DB_ETIMEOUT if not
+ * yet, or the solve's own error status. A ticket can be polled until done. */
+db_status db_server_poll(db_server* srv, uint64_t ticket, int timeout_us, double* latency_ms);
+/* Drain the queue, stop the scheduler and free everything. */
+db_status db_server_destroy(db_server* srv);
+
 /* ---- measurement ------------------------------------------------------------
  * Counters a context accumulates over its calls (reset by db_reset_stats):
  * kernel launches it issued, and for the LSQR kernel (the dominant one) its
@@ -152,11 +219,13 @@ db_status db_apply_L(int m, const void* x, void* q, db_precision prec, db_stream
 db_status db_apply_Lt(int m, const void* q, void* x, db_precision prec, db_stream stream);
 
 /* Restriction y = W^T x (m x m -> m/2 x m/2) and prolongation x = W y
- * (Sec. 4, W = W1 kron W1, periodic stride-2 filters). */
+ * (Sec. 4, W = W1 kron W1, periodic stride-2 filters). m and m_coarse must
+ * be powers of two (DB_EINVAL otherwise), m at least the filter length. */
 db_status db_restrict(int m, db_wavelet wavelet, const void* x, void* y, db_precision prec, db_stream stream);
 db_status db_prolong(int m_coarse, db_wavelet wavelet, const void* y, void* x, db_precision prec, db_stream stream);
 /* Approach D blockwise transfer (Sec. 4.2): Qx_f = W~1 Qx_c W1^T,
- * Qy_f = W1 Qy_c W~1^T on padded planes (2*m_c*m_c -> 2*m_f*m_f). */
+ * Qy_f = W1 Qy_c W~1^T on padded planes (2*m_c*m_c -> 2*m_f*m_f);
+ * m_coarse a power of two. */
 db_status db_aux_prolong(int m_coarse, db_wavelet wavelet, const void* qc, void* qf,
                          db_precision prec, db_stream stream);
 

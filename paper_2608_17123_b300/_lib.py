@@ -32,13 +32,25 @@ class DbOpts(C.Structure):
 class DbGcvOpts(C.Structure):
     _fields_ = [("grid_points", C.c_int), ("log10_gamma_lo", C.c_double), ("log10_gamma_hi", C.c_double),
                 ("refine_tol_log10", C.c_double), ("gcv_estimates", C.c_int), ("proj_dim", C.c_int),
-                ("proj_dim_max", C.c_int), ("gamma_fixed", C.c_double)]
+                ("proj_dim_max", C.c_int), ("gamma_fixed", C.c_double), ("exact_max_pixels", C.c_int)]
 
 
 class DbStats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("lsqr_launches", C.c_uint64), ("lsqr_ms", C.c_double),
                 ("lsqr_pixel_iters_irls", C.c_double), ("lsqr_pixel_iters_other", C.c_double),
                 ("gcv_calls", C.c_uint64), ("outer_iterations", C.c_uint64)]
+
+
+class DbRequest(C.Structure):
+    _fields_ = [("b", C.c_void_p), ("m", C.c_int), ("psf", C.c_void_p), ("psf_size", C.c_int),
+                ("solver", C.c_int), ("wavelet", C.c_int), ("levels", C.c_int), ("transfer", C.c_int),
+                ("x", C.c_void_p), ("mu_per_level", C.c_void_p), ("iters_per_level", C.c_void_p),
+                ("inner_iters_per_level", C.c_void_p)]
+
+
+class DbServerOpts(C.Structure):
+    _fields_ = [("max_resident", C.c_int), ("max_m", C.c_int), ("hbm_budget_bytes", C.c_size_t),
+                ("opts", DbOpts), ("gcv", DbGcvOpts)]
 
 
 class DeblurError(RuntimeError):
@@ -58,6 +70,11 @@ _SIGS = {
     "db_footprint_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(DbGcvOpts)]),
     "deblur_solve": (C.c_int, [_VP, _VP, C.c_int, _VP, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                C.POINTER(DbGcvOpts), C.POINTER(DbOpts), _VP, _VP, _VP, _VP, C.c_int, _VP]),
+    "deblur_solve_batch": (C.c_int, [_VP, C.c_int, _VP, C.POINTER(DbGcvOpts), C.POINTER(DbOpts), C.c_int, _VP]),
+    "db_server_create": (C.c_int, [_VP, C.POINTER(DbServerOpts), C.POINTER(_VP)]),
+    "db_server_submit": (C.c_int, [_VP, C.POINTER(DbRequest), C.POINTER(C.c_uint64)]),
+    "db_server_poll": (C.c_int, [_VP, C.c_uint64, C.c_int, C.POINTER(C.c_double)]),
+    "db_server_destroy": (C.c_int, [_VP]),
     "db_set_profiling": (C.c_int, [_VP, C.c_int]),
     "db_get_stats": (C.c_int, [_VP, C.POINTER(DbStats)]),
     "db_reset_stats": (C.c_int, [_VP]),

@@ -107,6 +107,38 @@ def deblur_solve(b, psf, solver="irls", wavelet="haar", levels=2, transfer="X", 
     return dict(x=from_colmajor(x, m), mu=list(mu), iters=[int(v) for v in it], inner=[int(v) for v in inner])
 
 
+def deblur_solve_batch(problems, precision="fp32", ctx=None, stream=None, **options):
+    """Batched solves. ``problems``: list of dicts with keys b (m x m array),
+    psf, solver, wavelet, levels, transfer. Returns a list of result dicts."""
+    ctx = ctx or default_context()
+    o, g = make_opts(precision, **options)
+    keep, reqs, outs = [], (L.DbRequest * len(problems))(), []
+    for i, pr in enumerate(problems):
+        b = np.asarray(pr["b"], dtype=np.float64)
+        m = b.shape[0]
+        psf = np.asarray(pr["psf"], dtype=np.float64)
+        lv = pr.get("levels", 2)
+        bb, pp = to_colmajor(b), to_colmajor(psf)
+        x = np.empty(m * m)
+        mu = np.zeros(lv)
+        it = np.zeros(lv, dtype=np.int32)
+        inner = np.zeros(lv, dtype=np.int32)
+        keep += [bb, pp, x, mu, it, inner]
+        r = reqs[i]
+        r.b, r.m, r.psf, r.psf_size = bb.ctypes.data, m, pp.ctypes.data, psf.shape[0]
+        r.solver = L.SOLVERS[pr.get("solver", "irls")]
+        r.wavelet = L.WAVELETS[pr.get("wavelet", "haar")]
+        r.levels = lv
+        r.transfer = L.TRANSFERS[pr.get("transfer", "X")]
+        r.x, r.mu_per_level, r.iters_per_level, r.inner_iters_per_level = (
+            x.ctypes.data, mu.ctypes.data, it.ctypes.data, inner.ctypes.data)
+        outs.append((m, x, mu, it, inner))
+    L.check(L.lib().deblur_solve_batch(ctx.handle, len(problems), reqs, C.byref(g), C.byref(o), 0,
+                                       _stream(stream)), ctx.handle)
+    return [dict(x=from_colmajor(x, m), mu=list(mu), iters=[int(v) for v in it], inner=[int(v) for v in inner])
+            for (m, x, mu, it, inner) in outs]
+
+
 def deblur_solve_device(b_dev, psf_dev, m, S, x_dev, solver="irls", wavelet="haar", levels=2, transfer="X",
                         precision="fp32", ctx=None, stream=None, **options):
     """Same call on device buffers (torch float64 CUDA tensors, column-major)."""
@@ -176,3 +208,59 @@ def gcv_select(psf, m, solver, b, aux0=None, aux1=None, ctx=None, stream=None, *
                                   _ptr(aux0), _ptr(aux1), C.byref(g), C.byref(gamma), _prec(b),
                                   _stream(stream)), ctx.handle)
     return gamma.value
+
+
+class Server:
+    """Continuous-batching solver (db_server_*): submit() returns a ticket at
+    once; poll() waits for it and returns (result dict, latency in ms)."""
+
+    def __init__(self, max_resident=8, max_m=1024, hbm_budget_bytes=0, ctx=None, **options):
+        self.ctx = ctx or Context(0)
+        o, g = make_opts("fp32", **options)
+        so = L.DbServerOpts()
+        so.max_resident, so.max_m, so.hbm_budget_bytes = max_resident, max_m, hbm_budget_bytes
+        so.opts, so.gcv = o, g
+        self.handle = C.c_void_p()
+        L.check(L.lib().db_server_create(self.ctx.handle, C.byref(so), C.byref(self.handle)), self.ctx.handle)
+        self._live = {}
+
+    def submit(self, b, psf, solver="irls", wavelet="haar", levels=2, transfer="X"):
+        b = np.asarray(b, dtype=np.float64)
+        m = b.shape[0]
+        psf = np.asarray(psf, dtype=np.float64)
+        bb, pp = to_colmajor(b), to_colmajor(psf)
+        x = np.empty(m * m)
+        mu = np.zeros(levels)
+        it = np.zeros(levels, dtype=np.int32)
+        inner = np.zeros(levels, dtype=np.int32)
+        r = L.DbRequest()
+        r.b, r.m, r.psf, r.psf_size = bb.ctypes.data, m, pp.ctypes.data, psf.shape[0]
+        r.solver, r.wavelet, r.levels = L.SOLVERS[solver], L.WAVELETS[wavelet], levels
+        r.transfer = L.TRANSFERS[transfer]
+        r.x, r.mu_per_level, r.iters_per_level, r.inner_iters_per_level = (
+            x.ctypes.data, mu.ctypes.data, it.ctypes.data, inner.ctypes.data)
+        t = C.c_uint64(0)
+        L.check(L.lib().db_server_submit(self.handle, C.byref(r), C.byref(t)), self.ctx.handle)
+        self._live[t.value] = (m, x, mu, it, inner, bb, pp, r)
+        return t.value
+
+    def poll(self, ticket, timeout_us=-1):
+        lat = C.c_double(0.0)
+        st = L.lib().db_server_poll(self.handle, ticket, timeout_us, C.byref(lat))
+        if st == 4:  # DB_ETIMEOUT
+            return None
+        L.check(st, self.ctx.handle)
+        m, x, mu, it, inner, _, _, _ = self._live.pop(ticket)
+        return dict(x=from_colmajor(x, m), mu=list(mu), iters=[int(v) for v in it],
+                    inner=[int(v) for v in inner]), lat.value
+
+    def close(self):
+        if self.handle:
+            L.lib().db_server_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda/atomic>
 #include <stdint.h>
 
 namespace db {
@@ -28,7 +29,9 @@ template <> __device__ __forceinline__ double store_cast<double, double>(double 
 template <> __device__ __forceinline__ float store_cast<float, float>(float v) { return v; }
 template <> __device__ __forceinline__ __nv_bfloat16 store_cast<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
 
-__device__ __forceinline__ int wrap(int i, int m) { int r = i % m; return r < 0 ? r + m : r; }
+// i mod m for a power-of-two m (every image side in this library is one),
+// correct for negative i.
+__device__ __forceinline__ int wrap(int i, int m) { return i & (m - 1); }
 
 // ---- reductions -------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
@@ -55,6 +58,53 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* scratch) {
   for (int k = 0; k < NV; ++k) {
     double s = (lane < nw) ? scratch[k * 32 + lane] : 0.0;
     v[k] = warp_sum(s);
+  }
+  __syncthreads();
+}
+
+// Compensated (error-free TwoSum) warp reduction of float partials: returns
+// hi + lo in double on every lane. Keeps the sum to about twice float
+// precision without FP64 arithmetic, whose rate is a small fraction of FP32
+// on this part.
+__device__ __forceinline__ double warp_sum_comp(float v) {
+  float s = v, c = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+    const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    const float t = s + s2;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (s2 - bp);
+    c = c + c2 + e;
+    s = t;
+  }
+  return (double)s + (double)c;
+}
+__device__ __forceinline__ double warp_sum_comp(double v) { return warp_sum(v); }
+
+// Block sum of NV per-thread partials (float or double); the result (double)
+// is valid in thread (0,0) only. `scratch` needs NV * 32 doubles. The warp
+// totals are combined by warp 0 with a fixed butterfly (no serial chain of
+// double additions).
+template <int NV, typename A>
+__device__ __forceinline__ void block_sum_to0(const A (&v)[NV], double (&out)[NV], double* scratch) {
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int nw = (blockDim.x * blockDim.y) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const double w = warp_sum_comp(v[k]);
+    if (lane == 0) scratch[k * 32 + wid] = w;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    double s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s[k] = lane < nw ? scratch[k * 32 + lane] : 0.0;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s[k] = warp_sum(s[k]);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = s[k];
   }
   __syncthreads();
 }

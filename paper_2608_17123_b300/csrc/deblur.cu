@@ -13,6 +13,15 @@
 #include <string>
 #include <vector>
 #include <algorithm>
+#include <type_traits>
+#include <atomic>
+#include <thread>
+#include <memory>
+#include <mutex>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <chrono>
 
 #include "../../include/deblur.h"
 #include "gcv.cuh"
@@ -48,6 +57,10 @@ struct Arena {
   char* base = nullptr;
   size_t cap = 0, off = 0;
   size_t budget = 0;
+  Arena() = default;
+  Arena(const Arena&) = delete;
+  Arena& operator=(const Arena&) = delete;
+  ~Arena() { if (base) cudaFree(base); }
   void reset() { off = 0; }
   void ensure(size_t bytes) {
     if (bytes <= cap) return;
@@ -76,7 +89,13 @@ struct db_context {
   Arena arena;
   std::string err;
   db_stats stats{};
+  std::atomic<uint64_t> n_launches{0}, n_gcv{0};
   int profiling = 0;
+  // factorisation of the last PSF (separable terms), reused while the PSF is unchanged
+  std::vector<double> psf_key;
+  double* psf_fr = nullptr;
+  double* psf_fc = nullptr;
+  int psf_nterms = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -84,7 +103,7 @@ struct db_context {
 // context can report how many of its kernels ran.
 static thread_local db_context* g_count_ctx = nullptr;
 static inline void count_launch() {
-  if (g_count_ctx) g_count_ctx->stats.kernel_launches++;
+  if (g_count_ctx) g_count_ctx->n_launches.fetch_add(1, std::memory_order_relaxed);
 }
 struct CountScope {
   db_context* prev;
@@ -127,6 +146,7 @@ struct Level {
   double* Bd_c = nullptr;
   Acc *br = nullptr, *bc = nullptr, *brT = nullptr, *bcT = nullptr;
   float* rho = nullptr;      // GCV symbol ratios [n]
+  double* b64 = nullptr;     // right-hand side in double (levels that use the exact GCV)
   // vectors
   T* b = nullptr;
   T* xa = nullptr;
@@ -178,6 +198,53 @@ __global__ void k_fill(size_t n, T* __restrict__ y, double v) {
 // ============================================================================
 // the solver for one storage type
 // ============================================================================
+// Device workspace of one GCV evaluation (Krylov basis, Gram matrices, the
+// small problem). A batch shares a few of these among its problems.
+template <typename Acc>
+struct GcvBufs {
+  Acc* gV = nullptr;
+  Acc *gt = nullptr, *gz = nullptr, *gy = nullptr, *gatb = nullptr, *gdtc = nullptr, *gknext = nullptr;
+  Acc *gcx = nullptr, *gcy = nullptr;
+  double *gGA = nullptr, *gGD = nullptr, *ggA = nullptr, *ggD = nullptr, *gh = nullptr, *gwork = nullptr;
+  double* gmdot_part = nullptr;
+  double *gAd = nullptr, *gbA = nullptr, *gbD = nullptr, *gh2 = nullptr;
+  float2* gpart2 = nullptr;
+  size_t gpart2_cap = 0;
+  int gkmax = 0;
+  size_t gn = 0;
+
+  static size_t bytes(size_t n0, int kmax, int exact_max, int nsm) {
+    size_t tot = n0 * sizeof(Acc) * (kmax + 9);
+    tot += (size_t)kmax * kmax * sizeof(double) * 8 + (size_t)kmax * 4096 * sizeof(double);
+    tot += (size_t)exact_max * exact_max * sizeof(double) + (size_t)kmax * 160 * sizeof(double);
+    tot += (size_t)(2 * kmax + 4) * std::max<size_t>((n0 + 2047) / 2048, (size_t)4 * nsm) * 8;
+    return tot + 64 * 4096;
+  }
+
+  void alloc(Arena& A, size_t n0, int kmax, int exact_max, int nsm) {
+    gkmax = kmax;
+    gn = n0;
+    gV = A.take<Acc>((size_t)kmax * n0);
+    gt = A.take<Acc>(n0); gz = A.take<Acc>(n0); gy = A.take<Acc>(n0);
+    gatb = A.take<Acc>(n0); gdtc = A.take<Acc>(n0); gknext = A.take<Acc>(n0);
+    gcx = A.take<Acc>(n0); gcy = A.take<Acc>(n0);
+    gGA = A.take<double>((size_t)kmax * kmax);
+    gGD = A.take<double>((size_t)kmax * kmax);
+    ggA = A.take<double>(kmax);
+    ggD = A.take<double>(kmax);
+    gh = A.take<double>(kmax);
+    gwork = A.take<double>((size_t)3 * kmax * kmax + (7 + 2 * SEL_MAXPTS + 8) * (size_t)kmax);
+    gAd = A.take<double>((size_t)std::max(exact_max, 1) * std::max(exact_max, 1));
+    gbA = A.take<double>(kmax);
+    gbD = A.take<double>(kmax);
+    gh2 = A.take<double>(kmax);
+    const size_t nch = std::max<size_t>((n0 + VCH_CHUNK - 1) / VCH_CHUNK, (size_t)4 * nsm);
+    gpart2_cap = (size_t)(2 * kmax + 4) * nch;
+    gpart2 = A.take<float2>(gpart2_cap);
+    gmdot_part = A.take<double>((size_t)kmax * 256);
+  }
+};
+
 template <typename T>
 struct Engine {
   using Acc = typename Traits<T>::Acc;
@@ -186,6 +253,7 @@ struct Engine {
   Hierarchy<T> H;
   db_opts o;
   db_gcv_opts go;
+  Arena* arena = nullptr;            // null: the context's arena
   // scratch shared by all levels
   double* d_part = nullptr;
   size_t part_cap = 0;
@@ -193,55 +261,93 @@ struct Engine {
   double* d_box = nullptr;           // small device mailbox
   GridBarrier* d_gb = nullptr;
   LsqrState* d_st = nullptr;
+  LsqrCoef<Acc>* d_coef = nullptr;
   LsqrProb<T, Acc>* d_prob = nullptr;
   int* d_tile_prob = nullptr;
-  // GCV workspace
+  // GCV workspace (owned or lent by a batch; see GcvBufs)
   Acc* gV = nullptr;
   Acc *gt = nullptr, *gz = nullptr, *gy = nullptr, *gatb = nullptr, *gdtc = nullptr, *gknext = nullptr;
   Acc *gcx = nullptr, *gcy = nullptr;
   double *gGA = nullptr, *gGD = nullptr, *ggA = nullptr, *ggD = nullptr, *gh = nullptr, *gwork = nullptr;
   double* gmdot_part = nullptr;
+  double *gAd = nullptr, *gbA = nullptr, *gbD = nullptr, *gh2 = nullptr;
+  float2* gpart2 = nullptr;
+  size_t gpart2_cap = 0;
   int gkmax = 0;
   size_t gn = 0;
+
+  void adopt(const GcvBufs<Acc>& b) {
+    gV = b.gV; gt = b.gt; gz = b.gz; gy = b.gy; gatb = b.gatb; gdtc = b.gdtc; gknext = b.gknext;
+    gcx = b.gcx; gcy = b.gcy; gGA = b.gGA; gGD = b.gGD; ggA = b.ggA; ggD = b.ggD; gh = b.gh; gwork = b.gwork;
+    gmdot_part = b.gmdot_part; gAd = b.gAd; gbA = b.gbA; gbD = b.gbD; gh2 = b.gh2; gpart2 = b.gpart2;
+    gpart2_cap = b.gpart2_cap; gkmax = b.gkmax; gn = b.gn;
+  }
 
   Engine(db_context* c, cudaStream_t s) : ctx(c), st(s) {}
 
   // ---------------------------------------------------------------- setup
-  static size_t footprint(int m, int levels, int S, const db_gcv_opts& g) {
+  static int gram_dim(const db_gcv_opts& g) {
+    return std::max(std::max(g.proj_dim_max, g.proj_dim), std::max(g.exact_max_pixels, 0)) + 2;
+  }
+
+  static size_t footprint_levels(int m, int levels, int S) {
     size_t tot = 0;
-    const int kmax = std::max(g.proj_dim_max, g.proj_dim) + 2;
-    size_t n0 = (size_t)m * m;
     for (int i = 0; i < levels; ++i) {
       int mi = m >> i;
       size_t n = (size_t)mi * mi;
-      tot += n * sizeof(T) * 16 + n * sizeof(float);
+      tot += n * sizeof(T) * 16 + n * sizeof(float) + n * sizeof(double);
       tot += (size_t)mi * (S + 64) * (sizeof(double) * 2 + sizeof(Acc) * 4) * S + 4096;
+      tot += (size_t)4 * S * m * 16;
     }
-    tot += n0 * sizeof(Acc) * (kmax + 9);
-    tot += (size_t)kmax * kmax * sizeof(double) * 6 + (size_t)kmax * 4096 * sizeof(double);
-    tot += 64ull << 20;
-    return tot;
+    return tot + ((size_t)m * m / 1024 + 64) * 3 * sizeof(double) + 8 * 4096 + ((size_t)2 * S * S + S) * 8;
   }
 
-  void build(const double* psf_dev, int S, int m, int levels, db_wavelet wv, const double* b_dev, bool with_vectors) {
-    Arena& A = ctx->arena;
+  static size_t footprint(int m, int levels, int S, const db_gcv_opts& g) {
+    return footprint_levels(m, levels, S) + GcvBufs<Acc>::bytes((size_t)m * m, gram_dim(g), g.exact_max_pixels, 160) +
+           (16ull << 20);
+  }
+
+  void build(const double* psf_dev, int S, int m, int levels, db_wavelet wv, const double* b_dev, bool with_vectors,
+             bool with_gcv = true) {
+    Arena& A = arena ? *arena : ctx->arena;
     H.S = S;
     H.levels = levels;
     H.lv.assign(levels, Level<T>());
-    // PSF factorisation (rank-revealing one-sided Jacobi SVD)
-    double* fr = A.take<double>((size_t)S * S);
-    double* fc = A.take<double>((size_t)S * S);
-    double* wk = A.take<double>((size_t)2 * S * S + S);
-    int* d_nt = A.take<int>(1);
-    { count_launch(); k_psf_svd<<<1, 128, 0, st>>>(S, psf_dev, 1e-13, d_nt, fr, fc, wk); }
-    CK(cudaGetLastError());
-    int nterms = 0;
-    CK(cudaMemcpyAsync(&nterms, d_nt, sizeof(int), cudaMemcpyDeviceToHost, st));
+    // PSF factorisation (rank-revealing one-sided Jacobi SVD), cached per PSF
+    std::vector<double> key((size_t)S * S + 1);
+    key[0] = (double)S;
+    CK(cudaMemcpyAsync(key.data() + 1, psf_dev, (size_t)S * S * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    REQUIRE(nterms >= 1, "PSF is zero");
+    const double* fr;
+    const double* fc;
+    int nterms = 0;
+    if (ctx->psf_fr && key == ctx->psf_key) {
+      fr = ctx->psf_fr;
+      fc = ctx->psf_fc;
+      nterms = ctx->psf_nterms;
+    } else {
+      if (ctx->psf_fr) { cudaFree(ctx->psf_fr); cudaFree(ctx->psf_fc); ctx->psf_fr = ctx->psf_fc = nullptr; }
+      ctx->psf_key.clear();
+      double *nfr = nullptr, *nfc = nullptr;
+      CK(cudaMalloc(&nfr, (size_t)S * S * sizeof(double)));
+      CK(cudaMalloc(&nfc, (size_t)S * S * sizeof(double)));
+      ctx->psf_fr = nfr;
+      ctx->psf_fc = nfc;
+      double* wk = A.take<double>((size_t)2 * S * S + S);
+      int* d_nt = A.take<int>(1);
+      { count_launch(); k_psf_svd<<<1, 256, 0, st>>>(S, psf_dev, 1e-13, d_nt, nfr, nfc, wk); }
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(&nterms, d_nt, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      REQUIRE(nterms >= 1, "PSF is zero");
+      ctx->psf_nterms = nterms;
+      ctx->psf_key = key;
+      fr = nfr;
+      fc = nfc;
+    }
     H.nterms = nterms;
     const Filter f = make_filter(wv);
-    const int kmax = std::max(go.proj_dim_max, go.proj_dim) + 2;
+    const int kmax = gram_dim(go);
     for (int i = 0; i < levels; ++i) {
       Level<T>& L = H.lv[i];
       L.m = m >> i;
@@ -284,6 +390,18 @@ struct Engine {
     }
     if (with_vectors && b_dev) {
       const size_t n0 = H.lv[0].n;
+      // double copy of b on every level small enough for the exact GCV
+      // (restricted in double from the input)
+      const double* bprev = b_dev;
+      for (int i = 0; i < levels; ++i) {
+        Level<T>& L = H.lv[i];
+        if (i > 0) {
+          double* bi = A.take<double>(L.n);
+          { count_launch(); k_restrict<double><<<grid_for(L.n, ctx->nsm), 256, 0, st>>>(H.lv[i - 1].m, f, bprev, bi); }
+          bprev = bi;
+        }
+        if ((long long)L.n <= (long long)go.exact_max_pixels) L.b64 = const_cast<double*>(bprev);
+      }
       { count_launch(); k_convert_in<T><<<grid_for(n0, ctx->nsm), 256, 0, st>>>(n0, b_dev, H.lv[0].b); }
       for (int i = 1; i < levels; ++i) {
         const Level<T>& P = H.lv[i - 1];
@@ -301,24 +419,15 @@ struct Engine {
     d_box = A.take<double>(64);
     d_gb = A.take<GridBarrier>(1);
     d_st = A.take<LsqrState>(1);
+    d_coef = A.take<LsqrCoef<Acc>>(1);
     d_prob = A.take<LsqrProb<T, Acc>>(1);
     d_tile_prob = A.take<int>(ntiles + 1);
     CK(cudaMemsetAsync(d_cnt, 0, 64 * sizeof(unsigned), st));
     CK(cudaMemsetAsync(d_gb, 0, sizeof(GridBarrier), st));
-    if (with_vectors) {
-      gkmax = kmax;
-      gn = n0;
-      gV = A.take<Acc>((size_t)kmax * n0);
-      gt = A.take<Acc>(n0); gz = A.take<Acc>(n0); gy = A.take<Acc>(n0);
-      gatb = A.take<Acc>(n0); gdtc = A.take<Acc>(n0); gknext = A.take<Acc>(n0);
-      gcx = A.take<Acc>(n0); gcy = A.take<Acc>(n0);
-      gGA = A.take<double>((size_t)kmax * kmax);
-      gGD = A.take<double>((size_t)kmax * kmax);
-      ggA = A.take<double>(kmax);
-      ggD = A.take<double>(kmax);
-      gh = A.take<double>(kmax);
-      gwork = A.take<double>((size_t)3 * kmax * kmax + 8 * kmax);
-      gmdot_part = A.take<double>((size_t)kmax * 256);
+    if (with_vectors && with_gcv) {
+      GcvBufs<Acc> b;
+      b.alloc(A, n0, kmax, go.exact_max_pixels, ctx->nsm);
+      adopt(b);
     }
   }
 
@@ -371,6 +480,7 @@ struct Engine {
     P.m = L.m;
     P.solver = solver;
     P.gamma = gamma;
+    P.sg = (Acc)std::sqrt(gamma);
     P.b = L.b;
     P.x0 = x0;
     P.a0x = L.a0x; P.a0y = L.a0y; P.a1x = L.a1x; P.a1y = L.a1y;
@@ -382,12 +492,13 @@ struct Engine {
     std::vector<int> tp(P.ntiles, 0);
     CK(cudaMemcpyAsync(d_tile_prob, tp.data(), sizeof(int) * tp.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(d_st, 0, sizeof(LsqrState), st));
+    CK(cudaMemsetAsync(d_coef, 0, sizeof(LsqrCoef<Acc>), st));
     CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned), st));
     CK(cudaMemsetAsync(d_gb, 0, sizeof(GridBarrier), st));
     LsqrCtl c;
     c.atol = o.lsqr_atol; c.btol = o.lsqr_btol; c.conlim = o.lsqr_conlim; c.maxit = o.lsqr_maxit;
     c.nprob = 1; c.ntiles = P.ntiles;
-    c.tile_prob = d_tile_prob; c.part = d_part; c.cnt = d_cnt; c.st = d_st; c.gb = d_gb;
+    c.tile_prob = d_tile_prob; c.part = d_part; c.cnt = d_cnt; c.st = d_st; c.gb = d_gb; c.coef = d_coef;
     c.limit_ns = 2000000000ull;
     const int sm = smem_bytes(P.op);
     auto kfn = k_lsqr<T, Acc>;
@@ -453,7 +564,7 @@ struct Engine {
 
   double gcv(const Level<T>& L, int solver, bool weighted, bool shifted) {
     if (go.gamma_fixed > 0) return go.gamma_fixed;
-    ctx->stats.gcv_calls++;
+    ctx->n_gcv.fetch_add(1, std::memory_order_relaxed);
     const size_t n = L.n;
     const int m = L.m;
     const int ld = gkmax;
@@ -485,7 +596,42 @@ struct Engine {
       CK(cudaStreamSynchronize(st));
       s = (h2[0] + h2[1]) / (2.0 * m * (m - 1));
     }
-    // v_0
+    if ((long long)n <= (long long)go.exact_max_pixels) {
+      // exact mode: dense pair, exact trace
+      const int nn = (int)n;
+      const int g2 = grid_for(n * n, ctx->nsm);
+      { count_launch(); k_dense_blur<<<g2, 256, 0, st>>>(m, H.nterms, L.dlo, L.w, L.Bd_r, L.Bd_c, gAd); }
+      { count_launch(); k_gram_dense<<<g2, 256, 0, st>>>(nn, gAd, gGA, ld); }
+      { count_launch(); k_dense_DtD<T><<<g2, 256, 0, st>>>(m, wx, wy, gGD, ld); }
+      double bnorm2_e = bnorm2;
+      if (L.b64) {
+        // A^T b and ||b||^2 in double from the double right-hand side
+        { count_launch(); k_dense_matvecT<<<grid_for(n, ctx->nsm), 256, 0, st>>>(nn, gAd, L.b64, gbA); }
+        dot_dev<double>(n, L.b64, L.b64, d_box + 30);
+        CK(cudaMemcpyAsync(&bnorm2_e, d_box + 30, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+      } else {
+        count_launch(); k_to_double<Acc><<<gsz, 256, 0, st>>>(n, gatb, gbA);
+      }
+      if (has_c) { count_launch(); k_to_double<Acc><<<gsz, 256, 0, st>>>(n, gdtc, gbD); }
+      else CK(cudaMemsetAsync(gbD, 0, n * sizeof(double), st));
+      CK(cudaGetLastError());
+      GcvSelectArgs a;
+      a.kk = nn; a.ld = ld; a.GA = gGA; a.GD = gGD; a.gA = gbA; a.gD = gbD;
+      a.bnorm2 = bnorm2_e; a.n = (double)n; a.s = 1.0; a.rho = L.rho; a.npix = nn; a.exact = 1;
+      a.lo = go.log10_gamma_lo; a.hi = go.log10_gamma_hi; a.tolx = go.refine_tol_log10;
+      a.npts = go.grid_points; a.max_ext = 2; a.work = gwork; a.out = d_box + 24;
+      { count_launch(); k_gcv_select<<<1, SEL_THREADS, 0, st>>>(a); }
+      CK(cudaGetLastError());
+      double gamma_e = 0.0;
+      CK(cudaMemcpyAsync(&gamma_e, d_box + 24, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      return gamma_e;
+    }
+    if constexpr (std::is_same<Acc, float>::value) {
+      return gcv_projected_fused(L, wx, wy, has_c, s, bnorm2, atb2);
+    } else {
+    // v_0 (double working precision: multi-launch path)
     CK(cudaMemcpyAsync(d_box + 20, &atb2, sizeof(double), cudaMemcpyHostToDevice, st));
     { count_launch(); k_scale_inv_sqrt<Acc><<<gsz, 256, 0, st>>>(n, gatb, d_box + 20, gV); }
     CK(cudaGetLastError());
@@ -549,7 +695,7 @@ struct Engine {
       // small problem + selection
       GcvSelectArgs a;
       a.kk = kk; a.ld = ld; a.GA = gGA; a.GD = gGD; a.gA = ggA; a.gD = ggD;
-      a.bnorm2 = bnorm2; a.n = (double)n; a.s = s; a.rho = L.rho; a.npix = (int)n;
+      a.bnorm2 = bnorm2; a.n = (double)n; a.s = s; a.rho = L.rho; a.npix = (int)n; a.exact = 0;
       a.lo = go.log10_gamma_lo; a.hi = go.log10_gamma_hi; a.tolx = go.refine_tol_log10;
       a.npts = go.grid_points; a.max_ext = 2; a.work = gwork; a.out = d_box + 24;
       { count_launch(); k_gcv_select<<<1, SEL_THREADS, 0, st>>>(a); }
@@ -558,6 +704,100 @@ struct Engine {
       CK(cudaStreamSynchronize(st));
       if (gamma_prev > 0 && std::fabs(gamma - gamma_prev) <= 1e-3 * gamma_prev) return gamma;
       if (2 * kdim > kcap || kdim >= (int)n || broke) return gamma;
+      gamma_prev = gamma;
+      kdim *= 2;
+    }
+    }
+  }
+
+  // Projected GCV with the fused Krylov kernels (float working precision):
+  // five launches per basis vector and no host round trip until selection.
+  void blur_dev(const Level<T>& L, bool tr, const Acc* x, Acc* y, const double* nrm2, Acc* xcopy) {
+    BandOp<Acc> op = L.op(H.nterms);
+    const int sm = smem_bytes(op);
+    if (sm > 48 * 1024) CK(cudaFuncSetAttribute(k_blur<Acc, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    const int nt = L.ntiles_side();
+    const int grid = std::min(nt * nt, ctx->nsm * 8);
+    { count_launch(); k_blur<Acc, Acc><<<grid, dim3(32, TY), sm, st>>>(op, tr ? 1 : 0, x, y, Acc(1), nrm2, xcopy); }
+    CK(cudaGetLastError());
+  }
+
+  double gcv_projected_fused(const Level<T>& L, const T* wx, const T* wy, bool has_c, double s, double bnorm2,
+                             double atb2) {
+    const size_t n = L.n;
+    const int m = L.m;
+    const int ld = gkmax;
+    // chunk of E*256 elements per block, E chosen to give ~2 blocks per SM
+    int E = VCH_E;
+    while (E > 1 && (n + (size_t)E * VCH_THREADS - 1) / ((size_t)E * VCH_THREADS) < (size_t)2 * ctx->nsm) E >>= 1;
+    const int nch = (int)((n + (size_t)E * VCH_THREADS - 1) / ((size_t)E * VCH_THREADS));
+    unsigned* cnt = d_cnt + 16;
+    float* V = reinterpret_cast<float*>(gV);
+    float* t = reinterpret_cast<float*>(gt);
+    // pending first direction: t = A^T b with ||t||^2 = atb2
+    CK(cudaMemcpyAsync(t, gatb, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(d_box + 21, &atb2, sizeof(double), cudaMemcpyHostToDevice, st));
+    const double dtc2 = has_c ? dot(n, gdtc, gdtc) : 0.0;
+    const int kcap = (int)std::min<size_t>((size_t)go.proj_dim_max, n);
+    int kdim = std::min<int>(go.proj_dim, kcap);
+    int cols = 0;
+    double gamma_prev = -1.0, gamma = 0.0;
+    for (;;) {
+      while (cols < kdim) {
+        const int j = cols;
+        // v_j = t / ||t|| (written by the A pass), z = A v_j, t = A^T z
+        blur_dev(L, false, gt, gz, d_box + 21, gV + (size_t)j * n);
+        blur_dev(L, true, gz, gt, nullptr, nullptr);
+        { count_launch(); k_gram_col<T><<<nch, VCH_THREADS, 0, st>>>(m, j, V, t, wx, wy,
+              reinterpret_cast<const float*>(gatb), has_c ? reinterpret_cast<const float*>(gdtc) : nullptr,
+              gpart2, cnt, gGA, gGD, ld, ggA, ggD, E); }
+        ++cols;
+        if (cols < kcap) {
+          // next direction: two classical Gram-Schmidt passes (the first reuses
+          // the Gram column G_A[i][j] = V_i . t)
+          { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, j + 1, V, n, gGA + j, ld, t,
+                VCH_UPDATE | VCH_DOTS, gpart2, cnt, gh, 1, nullptr, E); }
+          { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, j + 1, V, n, gh, 1, t,
+                VCH_UPDATE | VCH_NORM, gpart2, cnt, nullptr, 0, d_box + 21, E); }
+        }
+        CK(cudaGetLastError());
+      }
+      int kk = cols;
+      if (has_c) {
+        // shift direction orth(D^T c) in slot kk (two Gram-Schmidt passes)
+        float* vc = reinterpret_cast<float*>(gknext);
+        CK(cudaMemcpyAsync(vc, gdtc, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, kk, V, n, nullptr, 0, vc, VCH_DOTS, gpart2, cnt,
+              gh, 1, nullptr, E); }
+        { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, kk, V, n, gh, 1, vc, VCH_UPDATE | VCH_DOTS, gpart2,
+              cnt, gh2, 1, nullptr, E); }
+        { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, kk, V, n, gh2, 1, vc, VCH_UPDATE | VCH_NORM,
+              gpart2, cnt, nullptr, 0, d_box + 22, E); }
+        CK(cudaGetLastError());
+        double nc2 = 0.0;
+        CK(cudaMemcpyAsync(&nc2, d_box + 22, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (std::sqrt(nc2) > 1e-12 * std::sqrt(dtc2)) {
+          blur_dev(L, false, gknext, gz, d_box + 22, gV + (size_t)kk * n);
+          blur_dev(L, true, gz, gy, nullptr, nullptr);
+          { count_launch(); k_gram_col<T><<<nch, VCH_THREADS, 0, st>>>(m, kk, V, reinterpret_cast<float*>(gy), wx, wy,
+                reinterpret_cast<const float*>(gatb), reinterpret_cast<const float*>(gdtc), gpart2, cnt, gGA, gGD,
+                ld, ggA, ggD, E); }
+          CK(cudaGetLastError());
+          ++kk;
+        }
+      }
+      GcvSelectArgs a;
+      a.kk = kk; a.ld = ld; a.GA = gGA; a.GD = gGD; a.gA = ggA; a.gD = ggD;
+      a.bnorm2 = bnorm2; a.n = (double)n; a.s = s; a.rho = L.rho; a.npix = (int)n; a.exact = 0;
+      a.lo = go.log10_gamma_lo; a.hi = go.log10_gamma_hi; a.tolx = go.refine_tol_log10;
+      a.npts = go.grid_points; a.max_ext = 2; a.work = gwork; a.out = d_box + 24;
+      { count_launch(); k_gcv_select<<<1, SEL_THREADS, 0, st>>>(a); }
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(&gamma, d_box + 24, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (gamma_prev > 0 && std::fabs(gamma - gamma_prev) <= 1e-3 * gamma_prev) return gamma;
+      if (2 * kdim > kcap || kdim >= (int)n) return gamma;
       gamma_prev = gamma;
       kdim *= 2;
     }
@@ -605,36 +845,339 @@ struct Engine {
     *inner = tot_inner;
   }
 
-  void vcycle(db_solver solver, db_wavelet wv, db_transfer tr, double* mu, int* iters, int* inner) {
+  // Initial iterate and auxiliaries of level i (Alg. 4 / Sec. 4.1): the
+  // coarsest level starts as Approach I; a finer level from the coarser
+  // level's solution (Approach X) or auxiliary quantities (Approach D).
+  void init_level(int i, db_solver solver, db_wavelet wv, db_transfer tr) {
     const Filter f = make_filter(wv);
-    const int levels = H.levels;
-    for (int i = levels - 1; i >= 0; --i) {
-      Level<T>& L = H.lv[i];
-      const int g = grid_for(L.n, ctx->nsm);
-      if (i == levels - 1) {
-        { count_launch(); k_fill<T><<<g, 256, 0, st>>>(L.n, L.xa, 0.0); }
-        { count_launch(); k_aux_init<T><<<g, 256, 0, st>>>(L.m, solver, AUX_APPROACH_I, L.xa, L.a0x, L.a0y, L.a1x, L.a1y,
-                                          o.eps_irls, o.eps_mm, o.tau_sb); }
+    Level<T>& L = H.lv[i];
+    const int g = grid_for(L.n, ctx->nsm);
+    if (i == H.levels - 1) {
+      { count_launch(); k_fill<T><<<g, 256, 0, st>>>(L.n, L.xa, 0.0); }
+      { count_launch(); k_aux_init<T><<<g, 256, 0, st>>>(L.m, solver, AUX_APPROACH_I, L.xa, L.a0x, L.a0y, L.a1x,
+            L.a1y, o.eps_irls, o.eps_mm, o.tau_sb); }
+    } else {
+      const Level<T>& C = H.lv[i + 1];
+      if (tr == DB_APPROACH_X) {
+        { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.xa, L.xa, 0, 0); }
+        { count_launch(); k_aux_init<T><<<g, 256, 0, st>>>(L.m, solver, AUX_FROM_X, L.xa, L.a0x, L.a0y, L.a1x,
+              L.a1y, o.eps_irls, o.eps_mm, o.tau_sb); }
       } else {
-        const Level<T>& C = H.lv[i + 1];
-        if (tr == DB_APPROACH_X) {
-          { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.xa, L.xa, 0, 0); }
-          { count_launch(); k_aux_init<T><<<g, 256, 0, st>>>(L.m, solver, AUX_FROM_X, L.xa, L.a0x, L.a0y, L.a1x, L.a1y,
-                                            o.eps_irls, o.eps_mm, o.tau_sb); }
-        } else {
-          { count_launch(); k_fill<T><<<g, 256, 0, st>>>(L.n, L.xa, 0.0); }
-          { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.a0x, L.a0x, 1, 0); }
-          { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.a0y, L.a0y, 0, 1); }
-          if (solver == DB_SB) {
-            { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.a1x, L.a1x, 1, 0); }
-            { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.a1y, L.a1y, 0, 1); }
-          }
+        { count_launch(); k_fill<T><<<g, 256, 0, st>>>(L.n, L.xa, 0.0); }
+        { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.a0x, L.a0x, 1, 0); }
+        { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.a0y, L.a0y, 0, 1); }
+        if (solver == DB_SB) {
+          { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.a1x, L.a1x, 1, 0); }
+          { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.a1y, L.a1y, 0, 1); }
         }
       }
-      CK(cudaGetLastError());
+    }
+    CK(cudaGetLastError());
+  }
+
+  void vcycle(db_solver solver, db_wavelet wv, db_transfer tr, double* mu, int* iters, int* inner) {
+    const int levels = H.levels;
+    for (int i = levels - 1; i >= 0; --i) {
+      init_level(i, solver, wv, tr);
       const double tol = i > 0 ? o.tol_coarse : o.tol_fine;
       const bool twopass = (solver == DB_IRLS && levels >= 3 && i == 0);
-      level_solve(L, solver, tol, twopass, &mu[i], &iters[i], &inner[i]);
+      level_solve(H.lv[i], solver, tol, twopass, &mu[i], &iters[i], &inner[i]);
+    }
+  }
+
+  // x_new = x_old + delta and auxiliaries, without waiting; the two RC norms
+  // land in out[0..1].
+  void outer_update_async(Level<T>& L, int solver, const T* x_old, T* x_new, double* out) {
+    const int g = grid_for(L.n, ctx->nsm);
+    { count_launch(); k_outer_update<T><<<g, 256, 0, st>>>(L.m, solver, o.lsqr_warm_start, x_old, L.dlt, x_new,
+          L.a0x, L.a0y, L.a1x, L.a1y, o.eps_irls, o.eps_mm, o.tau_sb, d_part, d_cnt + 4, out); }
+    CK(cudaGetLastError());
+  }
+};
+
+// ============================================================================
+// batched solves: many V-cycles advanced together (one outer iteration of
+// every unfinished problem per scheduler step)
+// ============================================================================
+template <typename T>
+struct BatchSolver {
+  using Acc = typename Traits<T>::Acc;
+  struct Prob {
+    std::unique_ptr<Engine<T>> E;
+    db_solver solver;
+    db_wavelet wv;
+    db_transfer tr;
+    int levels = 0, level = 0, k = 0, inner = 0;
+    double gamma = 0.0;
+    bool done = false;
+    T* x = nullptr;
+    T* xn = nullptr;
+    std::vector<double> mu;
+    std::vector<int> iters, inners;
+  };
+  db_context* ctx;
+  cudaStream_t st;
+  db_opts o;
+  db_gcv_opts go;
+  std::vector<Prob> P;
+  std::vector<GcvBufs<Acc>> gbufs;
+  std::vector<cudaStream_t> wst;
+  LsqrProb<T, Acc>* d_probs = nullptr;
+  LsqrState* d_states = nullptr;
+  LsqrCoef<Acc>* d_coefs = nullptr;
+  int* d_tile_prob = nullptr;
+  double* d_part = nullptr;
+  GridBarrier* d_gb = nullptr;
+  double* d_rc = nullptr;
+  size_t max_tiles = 0;
+
+  BatchSolver(db_context* c, cudaStream_t s) : ctx(c), st(s) {}
+  ~BatchSolver() {
+    P.clear();
+    for (auto w : wst) cudaStreamDestroy(w);
+  }
+
+  static int workers_for(int count) { return std::max(1, std::min(count, 4)); }
+
+  static size_t footprint(int count, const db_request* r, const db_gcv_opts& g) {
+    size_t tot = 0, n0max = 0, tiles = 0;
+    for (int i = 0; i < count; ++i) {
+      tot += Engine<T>::footprint_levels(r[i].m, r[i].levels, r[i].psf_size) + (4ull << 20);
+      n0max = std::max(n0max, (size_t)r[i].m * r[i].m);
+      tiles += (size_t)((r[i].m + TM - 1) / TM) * ((r[i].m + TM - 1) / TM);
+    }
+    tot += (size_t)workers_for(count) * GcvBufs<Acc>::bytes(n0max, Engine<T>::gram_dim(g), g.exact_max_pixels, 160);
+    tot += (size_t)count * (sizeof(LsqrProb<T, Acc>) + sizeof(LsqrState) + sizeof(LsqrCoef<Acc>) + 4 * 256 + 64);
+    tot += tiles * (3 * sizeof(double) + sizeof(int)) + (16ull << 20);
+    return tot;
+  }
+
+  // Shared buffers: batched-LSQR tables for up to max_probs problems and
+  // max_tiles tiles, and the GCV workspaces of the worker streams.
+  void alloc_shared(Arena& A, int max_probs, size_t tiles, size_t n0max, int nworkers) {
+    max_tiles = tiles;
+    gbufs.resize(nworkers);
+    for (int w = 0; w < nworkers; ++w) gbufs[w].alloc(A, n0max, Engine<T>::gram_dim(go), go.exact_max_pixels, ctx->nsm);
+    wst.resize(nworkers);
+    for (int w = 0; w < nworkers; ++w) CK(cudaStreamCreateWithFlags(&wst[w], cudaStreamNonBlocking));
+    d_probs = A.take<LsqrProb<T, Acc>>(max_probs);
+    d_states = A.take<LsqrState>(max_probs);
+    d_coefs = A.take<LsqrCoef<Acc>>(max_probs);
+    d_tile_prob = A.take<int>(max_tiles + 1);
+    d_part = A.take<double>(3 * max_tiles + 3);
+    d_gb = A.take<GridBarrier>(1);
+    d_rc = A.take<double>(2 * (size_t)max_probs);
+    P.resize(max_probs);
+    for (auto& q : P) q.done = true;
+  }
+
+  // Put a problem into slot i and start its coarsest level.
+  void add_problem(int i, const db_request& r, const double* b_dev, const double* psf_dev, Arena* own) {
+    Prob& q = P[i];
+    q.E.reset(new Engine<T>(ctx, st));
+    q.E->o = o;
+    q.E->go = go;
+    q.E->arena = own;
+    q.solver = r.solver;
+    q.wv = r.wavelet;
+    q.levels = r.levels;
+    q.tr = q.levels == 1 ? DB_APPROACH_I : r.transfer;
+    q.E->build(psf_dev, r.psf_size, r.m, q.levels, q.wv, b_dev, true, false);
+    q.mu.assign(q.levels, 0.0);
+    q.iters.assign(q.levels, 0);
+    q.inners.assign(q.levels, 0);
+    q.level = q.levels - 1;
+    q.done = false;
+    start_level(q);
+  }
+
+  void setup(int count, const db_request* reqs, const double* const* b_dev, const double* const* psf_dev) {
+    size_t n0max = 0, tiles = 0;
+    for (int i = 0; i < count; ++i) {
+      n0max = std::max(n0max, (size_t)reqs[i].m * reqs[i].m);
+      tiles += (size_t)((reqs[i].m + TM - 1) / TM) * ((reqs[i].m + TM - 1) / TM);
+    }
+    alloc_shared(ctx->arena, count, tiles, n0max, workers_for(count));
+    for (int i = 0; i < count; ++i) add_problem(i, reqs[i], b_dev[i], psf_dev[i], nullptr);
+    CK(cudaStreamSynchronize(st));
+  }
+
+  void start_level(Prob& q) {
+    q.E->st = st;
+    q.E->init_level(q.level, q.solver, q.wv, q.tr);
+    Level<T>& L = q.E->H.lv[q.level];
+    q.x = L.xa;
+    q.xn = L.xb;
+    q.k = 0;
+    q.inner = 0;
+  }
+
+  // 0: no GCV this iteration; otherwise 1 + (weighted ? 1 : 0) + (shifted ? 2 : 0)
+  int gcv_kind(const Prob& q) const {
+    if (q.solver == DB_IRLS) {
+      const bool twopass = q.levels >= 3 && q.level == 0;
+      if (!twopass) return 1 + 1;
+      if (q.k == 0) return 1;
+      if (q.k == 3) return 1 + 1;
+      return 0;
+    }
+    return q.k < go.gcv_estimates ? 1 + 2 : 0;
+  }
+
+  void run_gcvs(const std::vector<int>& need) {
+    if (need.empty()) return;
+    const int nw = (int)gbufs.size();
+    std::vector<std::thread> th;
+    std::vector<DbError> errs(nw);
+    std::vector<int> failed(nw, 0);
+    for (int w = 0; w < nw; ++w) {
+      th.emplace_back([&, w]() {
+        CountScope cs(ctx);
+        try {
+          CK(cudaSetDevice(ctx->device));
+          for (size_t j = w; j < need.size(); j += nw) {
+            Prob& q = P[need[j]];
+            const int kind = gcv_kind(q);
+            q.E->adopt(gbufs[w]);
+            q.E->st = wst[w];
+            // the level's x and auxiliaries were written on the main stream,
+            // which the scheduler has synchronised before this point
+            q.gamma = q.E->gcv(q.E->H.lv[q.level], q.solver, (kind - 1) & 1, ((kind - 1) & 2) != 0);
+            q.E->st = st;
+          }
+        } catch (DbError& e) {
+          errs[w] = e;
+          failed[w] = 1;
+        }
+      });
+    }
+    for (auto& t : th) t.join();
+    for (int w = 0; w < nw; ++w)
+      if (failed[w]) throw errs[w];
+  }
+
+  void lsqr_batch(const std::vector<int>& act, std::vector<int>& its) {
+    std::vector<LsqrProb<T, Acc>> hp(act.size());
+    std::vector<int> tp;
+    int sm = 0;
+    for (size_t j = 0; j < act.size(); ++j) {
+      Prob& q = P[act[j]];
+      Engine<T>& E = *q.E;
+      Level<T>& L = E.H.lv[q.level];
+      LsqrProb<T, Acc>& X = hp[j];
+      X.op = L.op(E.H.nterms);
+      X.m = L.m;
+      X.solver = q.solver;
+      X.gamma = q.gamma;
+      X.sg = (Acc)std::sqrt(q.gamma);
+      X.b = L.b;
+      X.x0 = o.lsqr_warm_start ? q.x : nullptr;
+      X.a0x = L.a0x; X.a0y = L.a0y; X.a1x = L.a1x; X.a1y = L.a1y;
+      X.uA = L.uA; X.uLx = L.uLx; X.uLy = L.uLy; X.v = L.v; X.w = L.wv; X.dlt = L.dlt;
+      X.nt = L.ntiles_side();
+      X.ntiles = X.nt * X.nt;
+      X.tile_begin = (int)tp.size();
+      for (int t = 0; t < X.ntiles; ++t) tp.push_back((int)j);
+      sm = std::max(sm, E.smem_bytes(X.op));
+    }
+    const int np = (int)act.size();
+    CK(cudaMemcpyAsync(d_probs, hp.data(), sizeof(LsqrProb<T, Acc>) * np, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_tile_prob, tp.data(), sizeof(int) * tp.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(d_states, 0, sizeof(LsqrState) * np, st));
+    CK(cudaMemsetAsync(d_coefs, 0, sizeof(LsqrCoef<Acc>) * np, st));
+    CK(cudaMemsetAsync(d_gb, 0, sizeof(GridBarrier), st));
+    LsqrCtl c;
+    c.atol = o.lsqr_atol; c.btol = o.lsqr_btol; c.conlim = o.lsqr_conlim; c.maxit = o.lsqr_maxit;
+    c.nprob = np; c.ntiles = (int)tp.size();
+    c.tile_prob = d_tile_prob; c.part = d_part; c.cnt = nullptr; c.st = d_states; c.gb = d_gb; c.coef = d_coefs;
+    c.limit_ns = 2000000000ull;
+    auto kfn = k_lsqr<T, Acc>;
+    if (sm > 48 * 1024) CK(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, sm));
+    REQUIRE(per_sm >= 1, "LSQR kernel does not fit on an SM");
+    const int grid = std::max(1, std::min((int)tp.size(), per_sm * ctx->nsm));
+    const LsqrProb<T, Acc>* pp = d_probs;
+    void* args[] = {(void*)&pp, (void*)&c};
+    if (ctx->profiling) CK(cudaEventRecord(ctx->ev0, st));
+    count_launch();
+    CK(cudaLaunchCooperativeKernel((const void*)kfn, dim3(grid), dim3(32, TY), args, sm, st));
+    if (ctx->profiling) CK(cudaEventRecord(ctx->ev1, st));
+    std::vector<LsqrState> S(np);
+    GridBarrier gbh;
+    CK(cudaMemcpyAsync(S.data(), d_states, sizeof(LsqrState) * np, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&gbh, d_gb, sizeof(gbh), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (gbh.error) throw DbError{DB_ETIMEOUT, "LSQR grid barrier timed out"};
+    its.resize(np);
+    ctx->stats.lsqr_launches++;
+    for (int j = 0; j < np; ++j) {
+      its[j] = S[j].its;
+      const Prob& q = P[act[j]];
+      const double pix = (double)(S[j].its + 1) * (double)q.E->H.lv[q.level].n;
+      if (q.solver == DB_IRLS) ctx->stats.lsqr_pixel_iters_irls += pix;
+      else ctx->stats.lsqr_pixel_iters_other += pix;
+    }
+    if (ctx->profiling) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+      ctx->stats.lsqr_ms += ms;
+    }
+  }
+
+  // One scheduler step: one outer iteration of every unfinished problem.
+  // Returns the slots whose finest level completed in this step.
+  std::vector<int> step() {
+    std::vector<int> act, need, finished;
+    for (int i = 0; i < (int)P.size(); ++i)
+      if (!P[i].done) {
+        act.push_back(i);
+        if (gcv_kind(P[i])) need.push_back(i);
+      }
+    if (act.empty()) return finished;
+    run_gcvs(need);
+    std::vector<int> its;
+    lsqr_batch(act, its);
+    for (size_t j = 0; j < act.size(); ++j) {
+      Prob& q = P[act[j]];
+      q.E->outer_update_async(q.E->H.lv[q.level], q.solver, q.x, q.xn, d_rc + 2 * act[j]);
+    }
+    std::vector<double> rc(2 * P.size());
+    CK(cudaMemcpyAsync(rc.data(), d_rc, sizeof(double) * rc.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->stats.outer_iterations += act.size();
+    for (size_t j = 0; j < act.size(); ++j) {
+      Prob& q = P[act[j]];
+      const int i = act[j];
+      q.inner += its[j];
+      std::swap(q.x, q.xn);
+      ++q.k;
+      const double r = rc[2 * i + 1] == 0.0 ? INFINITY : std::sqrt(rc[2 * i]) / std::sqrt(rc[2 * i + 1]);
+      const double tol = q.level > 0 ? o.tol_coarse : o.tol_fine;
+      if (r < tol || q.k >= o.kmax) {
+        Level<T>& L = q.E->H.lv[q.level];
+        if (q.x != L.xa) CK(cudaMemcpyAsync(L.xa, q.x, L.n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        q.mu[q.level] = q.gamma;
+        q.iters[q.level] = q.k;
+        q.inners[q.level] = q.inner;
+        if (q.level == 0) {
+          q.done = true;
+          finished.push_back(i);
+        } else {
+          --q.level;
+          start_level(q);
+        }
+      }
+    }
+    return finished;
+  }
+
+  void run() {
+    for (;;) {
+      bool any = false;
+      for (auto& q : P) any |= !q.done;
+      if (!any) break;
+      step();
     }
   }
 };
@@ -652,7 +1195,7 @@ extern "C" void db_default_opts(db_opts* o, db_gcv_opts* g) {
   if (g) {
     g->grid_points = 50; g->log10_gamma_lo = -10.0; g->log10_gamma_hi = 2.0;
     g->refine_tol_log10 = 1e-5; g->gcv_estimates = 3; g->proj_dim = 40; g->proj_dim_max = 160;
-    g->gamma_fixed = 0.0;
+    g->gamma_fixed = 0.0; g->exact_max_pixels = 256;
   }
 }
 
@@ -696,12 +1239,16 @@ extern "C" db_status db_set_profiling(db_context* c, int on) {
 extern "C" db_status db_get_stats(db_context* c, db_stats* out) {
   if (!c || !out) return DB_EINVAL;
   *out = c->stats;
+  out->kernel_launches = c->n_launches.load();
+  out->gcv_calls = c->n_gcv.load();
   return DB_OK;
 }
 
 extern "C" db_status db_reset_stats(db_context* c) {
   if (!c) return DB_EINVAL;
   c->stats = db_stats{};
+  c->n_launches = 0;
+  c->n_gcv = 0;
   return DB_OK;
 }
 
@@ -710,6 +1257,8 @@ extern "C" db_status db_context_destroy(db_context* c) {
   cudaSetDevice(c->device);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->psf_fr) cudaFree(c->psf_fr);
+  if (c->psf_fc) cudaFree(c->psf_fc);
   if (c->arena.base) cudaFree(c->arena.base);
   delete c;
   return DB_OK;
@@ -764,7 +1313,9 @@ extern "C" db_status deblur_solve(db_context* ctx, const double* b, int m, const
     db_default_opts(&o, &g);
     if (opts) o = *opts;
     if (gcv) g = *gcv;
-    REQUIRE(g.proj_dim >= 1 && g.proj_dim_max >= g.proj_dim && g.grid_points >= 3, "bad GCV options");
+    REQUIRE(g.proj_dim >= 1 && g.proj_dim_max >= g.proj_dim && g.grid_points >= 3 && g.grid_points <= 64,
+            "bad GCV options");
+    REQUIRE(g.exact_max_pixels >= 0 && g.exact_max_pixels <= 1024, "exact_max_pixels out of range");
     REQUIRE(o.kmax >= 1 && o.lsqr_maxit >= 1, "bad iteration limits");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
@@ -807,6 +1358,316 @@ extern "C" db_status deblur_solve(db_context* ctx, const double* b, int m, const
     ctx->err = e.msg;
     return e.st;
   }
+}
+
+template <typename T>
+static void run_batch(db_context* ctx, cudaStream_t st, int count, const db_request* reqs, const db_gcv_opts& g,
+                      const db_opts& o, const double* const* b_dev, const double* const* psf_dev,
+                      double* const* x_dev) {
+  BatchSolver<T> B(ctx, st);
+  B.o = o;
+  B.go = g;
+  ctx->arena.ensure(BatchSolver<T>::footprint(count, reqs, g));
+  ctx->arena.reset();
+  B.setup(count, reqs, b_dev, psf_dev);
+  B.run();
+  for (int i = 0; i < count; ++i) {
+    auto& q = B.P[i];
+    const size_t n = (size_t)reqs[i].m * reqs[i].m;
+    { count_launch(); k_convert_out<T><<<grid_for(n, ctx->nsm), 256, 0, st>>>(n, q.E->H.lv[0].xa, x_dev[i]); }
+    for (int l = 0; l < q.levels; ++l) {
+      reqs[i].mu_per_level[l] = q.mu[l];
+      reqs[i].iters_per_level[l] = q.iters[l];
+      if (reqs[i].inner_iters_per_level) reqs[i].inner_iters_per_level[l] = q.inners[l];
+    }
+  }
+  CK(cudaGetLastError());
+}
+
+extern "C" db_status deblur_solve_batch(db_context* ctx, int count, const db_request* reqs, const db_gcv_opts* gcv,
+                                        const db_opts* opts, int on_device, db_stream stream) {
+  if (!ctx) return DB_EINVAL;
+  CountScope count_scope(ctx);
+  std::vector<double*> tmp;
+  cudaStream_t st = (cudaStream_t)stream;
+  try {
+    REQUIRE(count >= 1 && reqs, "empty batch");
+    db_opts o;
+    db_gcv_opts g;
+    db_default_opts(&o, &g);
+    if (opts) o = *opts;
+    if (gcv) g = *gcv;
+    REQUIRE(g.proj_dim >= 1 && g.proj_dim_max >= g.proj_dim && g.grid_points >= 3 && g.grid_points <= 64,
+            "bad GCV options");
+    for (int i = 0; i < count; ++i) {
+      const db_request& r = reqs[i];
+      REQUIRE(r.b && r.psf && r.x && r.mu_per_level && r.iters_per_level, "null pointer in a request");
+      validate(r.m, r.psf_size, r.levels, r.wavelet);
+      REQUIRE(r.solver >= DB_IRLS && r.solver <= DB_SB, "unknown solver");
+      REQUIRE(r.transfer >= DB_APPROACH_I && r.transfer <= DB_APPROACH_D, "unknown transfer strategy");
+    }
+    CK(cudaSetDevice(ctx->device));
+    std::vector<const double*> bd(count), pd(count);
+    std::vector<double*> xd(count);
+    for (int i = 0; i < count; ++i) {
+      const db_request& r = reqs[i];
+      const size_t n = (size_t)r.m * r.m, ps = (size_t)r.psf_size * r.psf_size;
+      if (on_device) {
+        bd[i] = r.b; pd[i] = r.psf; xd[i] = r.x;
+      } else {
+        double *b_, *p_, *x_;
+        CK(cudaMallocAsync((void**)&b_, n * sizeof(double), st)); tmp.push_back(b_);
+        CK(cudaMallocAsync((void**)&p_, ps * sizeof(double), st)); tmp.push_back(p_);
+        CK(cudaMallocAsync((void**)&x_, n * sizeof(double), st)); tmp.push_back(x_);
+        CK(cudaMemcpyAsync(b_, r.b, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(p_, r.psf, ps * sizeof(double), cudaMemcpyHostToDevice, st));
+        bd[i] = b_; pd[i] = p_; xd[i] = x_;
+      }
+    }
+    if (o.precision == DB_PREC_FP64) run_batch<double>(ctx, st, count, reqs, g, o, bd.data(), pd.data(), xd.data());
+    else if (o.precision == DB_PREC_BF16) run_batch<__nv_bfloat16>(ctx, st, count, reqs, g, o, bd.data(), pd.data(), xd.data());
+    else run_batch<float>(ctx, st, count, reqs, g, o, bd.data(), pd.data(), xd.data());
+    if (!on_device) {
+      for (int i = 0; i < count; ++i)
+        CK(cudaMemcpyAsync(reqs[i].x, xd[i], (size_t)reqs[i].m * reqs[i].m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    for (double* t : tmp) cudaFreeAsync(t, st);
+    CK(cudaStreamSynchronize(st));
+    return DB_OK;
+  } catch (DbError& e) {
+    for (double* t : tmp) cudaFreeAsync(t, st);
+    cudaStreamSynchronize(st);
+    ctx->err = e.msg;
+    return e.st;
+  }
+}
+
+
+// ============================================================================
+// serving loop
+// ============================================================================
+struct ServerJob {
+  uint64_t ticket = 0;
+  db_request req{};
+  std::vector<double> b, psf;
+  std::unique_ptr<Arena> arena;
+  double* dev_b = nullptr;
+  double* dev_psf = nullptr;
+  double* dev_x = nullptr;
+  size_t bytes = 0;
+  int slot = -1;
+  bool done = false;
+  db_status status = DB_OK;
+  std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+struct db_server {
+  db_context* ctx = nullptr;
+  db_server_opts opts{};
+  cudaStream_t st = nullptr;
+  std::thread th;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stopping = false;
+  uint64_t next_ticket = 1;
+  std::deque<ServerJob*> queue;
+  std::map<uint64_t, std::unique_ptr<ServerJob>> jobs;
+  Arena shared;                      // batched-LSQR tables and GCV workspaces
+  std::unique_ptr<BatchSolver<float>> B;
+  std::vector<ServerJob*> slots;
+  size_t bytes_in_use = 0;
+  std::string fatal;
+
+  static size_t job_bytes(const db_request& r) {
+    return Engine<float>::footprint_levels(r.m, r.levels, r.psf_size) + (4ull << 20);
+  }
+
+  void loop() {
+    CountScope cs(ctx);
+    cudaSetDevice(ctx->device);
+    for (;;) {
+      // admission at a step boundary
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        bool any_resident = false;
+        for (auto* j : slots) any_resident |= (j != nullptr);
+        if (!any_resident && queue.empty()) {
+          if (stopping) return;
+          cv_work.wait(lk, [&] { return stopping || !queue.empty(); });
+          if (stopping && queue.empty()) return;
+        }
+        while (!queue.empty()) {
+          ServerJob* j = queue.front();
+          int free_slot = -1;
+          for (int i = 0; i < (int)slots.size(); ++i)
+            if (!slots[i]) { free_slot = i; break; }
+          if (free_slot < 0) break;
+          if (opts.hbm_budget_bytes && bytes_in_use + j->bytes > opts.hbm_budget_bytes && bytes_in_use > 0) break;
+          queue.pop_front();
+          lk.unlock();
+          try {
+            const size_t n = (size_t)j->req.m * j->req.m, ps = (size_t)j->req.psf_size * j->req.psf_size;
+            j->arena.reset(new Arena());
+            j->arena->ensure(j->bytes + 3 * n * sizeof(double) + ps * sizeof(double) + 4096);
+            j->dev_b = j->arena->take<double>(n);
+            j->dev_psf = j->arena->take<double>(ps);
+            j->dev_x = j->arena->take<double>(n);
+            CK(cudaMemcpyAsync(j->dev_b, j->b.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(j->dev_psf, j->psf.data(), ps * sizeof(double), cudaMemcpyHostToDevice, st));
+            B->add_problem(free_slot, j->req, j->dev_b, j->dev_psf, j->arena.get());
+            lk.lock();
+            slots[free_slot] = j;
+            j->slot = free_slot;
+            bytes_in_use += j->bytes;
+          } catch (DbError& e) {
+            lk.lock();
+            j->status = e.st;
+            j->done = true;
+            j->t_done = std::chrono::steady_clock::now();
+            j->arena.reset();
+            cv_done.notify_all();
+          }
+        }
+      }
+      // one scheduler step over the resident solves
+      std::vector<int> fin;
+      try {
+        fin = B->step();
+      } catch (DbError& e) {
+        std::lock_guard<std::mutex> lk(mu);
+        fatal = e.msg;
+        for (int i = 0; i < (int)slots.size(); ++i)
+          if (slots[i]) {
+            ServerJob* j = slots[i];
+            j->status = e.st;
+            j->done = true;
+            j->t_done = std::chrono::steady_clock::now();
+            B->P[i].done = true;
+            B->P[i].E.reset();
+            j->arena.reset();
+            slots[i] = nullptr;
+          }
+        bytes_in_use = 0;
+        cv_done.notify_all();
+        continue;
+      }
+      for (int i : fin) {
+        ServerJob* j = slots[i];
+        auto& q = B->P[i];
+        const size_t n = (size_t)j->req.m * j->req.m;
+        try {
+          { count_launch(); k_convert_out<float><<<grid_for(n, ctx->nsm), 256, 0, st>>>(n, q.E->H.lv[0].xa, j->dev_x); }
+          CK(cudaMemcpyAsync(j->req.x, j->dev_x, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+          CK(cudaStreamSynchronize(st));
+          for (int l = 0; l < q.levels; ++l) {
+            j->req.mu_per_level[l] = q.mu[l];
+            j->req.iters_per_level[l] = q.iters[l];
+            if (j->req.inner_iters_per_level) j->req.inner_iters_per_level[l] = q.inners[l];
+          }
+        } catch (DbError& e) {
+          j->status = e.st;
+        }
+        q.E.reset();
+        std::lock_guard<std::mutex> lk(mu);
+        j->arena.reset();
+        bytes_in_use -= j->bytes;
+        slots[i] = nullptr;
+        j->done = true;
+        j->t_done = std::chrono::steady_clock::now();
+        cv_done.notify_all();
+      }
+    }
+  }
+};
+
+extern "C" db_status db_server_create(db_context* ctx, const db_server_opts* o, db_server** out) {
+  if (!ctx || !o || !out) return DB_EINVAL;
+  CountScope count_scope(ctx);
+  try {
+    REQUIRE(o->max_resident >= 1 && o->max_resident <= 256, "max_resident out of range");
+    REQUIRE(o->max_m >= 8 && (o->max_m & (o->max_m - 1)) == 0, "max_m must be a power of two");
+    CK(cudaSetDevice(ctx->device));
+    std::unique_ptr<db_server> s(new db_server());
+    s->ctx = ctx;
+    s->opts = *o;
+    s->opts.opts.precision = DB_PREC_FP32;
+    CK(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
+    s->B.reset(new BatchSolver<float>(ctx, s->st));
+    s->B->o = s->opts.opts;
+    s->B->go = s->opts.gcv;
+    const size_t n0max = (size_t)o->max_m * o->max_m;
+    const size_t tiles = (size_t)o->max_resident * ((o->max_m + TM - 1) / TM) * ((o->max_m + TM - 1) / TM);
+    const int nw = BatchSolver<float>::workers_for(o->max_resident);
+    s->shared.ensure((size_t)nw * GcvBufs<float>::bytes(n0max, Engine<float>::gram_dim(s->opts.gcv),
+                                                       s->opts.gcv.exact_max_pixels, 160) +
+                     tiles * 40 + (size_t)o->max_resident * 4096 + (16ull << 20));
+    s->B->alloc_shared(s->shared, o->max_resident, tiles, n0max, nw);
+    s->slots.assign(o->max_resident, nullptr);
+    db_server* raw = s.release();
+    raw->th = std::thread([raw] { raw->loop(); });
+    *out = raw;
+    return DB_OK;
+  } catch (DbError& e) {
+    ctx->err = e.msg;
+    return e.st;
+  }
+}
+
+extern "C" db_status db_server_submit(db_server* s, const db_request* r, uint64_t* ticket) {
+  if (!s || !r || !ticket) return DB_EINVAL;
+  try {
+    REQUIRE(r->b && r->psf && r->x && r->mu_per_level && r->iters_per_level, "null pointer in the request");
+    validate(r->m, r->psf_size, r->levels, r->wavelet);
+    REQUIRE(r->m <= s->opts.max_m, "image larger than the server's max_m");
+    REQUIRE(r->solver >= DB_IRLS && r->solver <= DB_SB, "unknown solver");
+    REQUIRE(r->transfer >= DB_APPROACH_I && r->transfer <= DB_APPROACH_D, "unknown transfer strategy");
+    std::unique_ptr<ServerJob> j(new ServerJob());
+    j->req = *r;
+    j->b.assign(r->b, r->b + (size_t)r->m * r->m);
+    j->psf.assign(r->psf, r->psf + (size_t)r->psf_size * r->psf_size);
+    j->bytes = db_server::job_bytes(*r);
+    j->t_submit = std::chrono::steady_clock::now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stopping) return DB_EBUSY;
+    j->ticket = s->next_ticket++;
+    *ticket = j->ticket;
+    s->queue.push_back(j.get());
+    s->jobs[j->ticket] = std::move(j);
+    s->cv_work.notify_one();
+    return DB_OK;
+  } catch (DbError& e) {
+    s->ctx->err = e.msg;
+    return e.st;
+  }
+}
+
+extern "C" db_status db_server_poll(db_server* s, uint64_t ticket, int timeout_us, double* latency_ms) {
+  if (!s) return DB_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(ticket);
+  if (it == s->jobs.end()) return DB_EINVAL;
+  ServerJob* j = it->second.get();
+  auto ready = [&] { return j->done; };
+  if (timeout_us < 0) s->cv_done.wait(lk, ready);
+  else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) return DB_ETIMEOUT;
+  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count();
+  if (j->status != DB_OK && !s->fatal.empty()) s->ctx->err = s->fatal;
+  return j->status;
+}
+
+extern "C" db_status db_server_destroy(db_server* s) {
+  if (!s) return DB_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stopping = true;
+    s->cv_work.notify_all();
+  }
+  if (s->th.joinable()) s->th.join();
+  cudaSetDevice(s->ctx->device);
+  s->B.reset();
+  if (s->st) cudaStreamDestroy(s->st);
+  delete s;   // frees the shared arena
+  return DB_OK;
 }
 
 // ---- operator-level entry points ---------------------------------------------
@@ -891,7 +1752,7 @@ extern "C" db_status db_apply_Lt(int m, const void* q, void* x, db_precision pre
 
 extern "C" db_status db_restrict(int m, db_wavelet wv, const void* x, void* y, db_precision prec, db_stream stream) {
   return simple_call([&] {
-    REQUIRE(m >= 4 && (m & 1) == 0 && x && y, "bad arguments");
+    REQUIRE(m >= 4 && (m & (m - 1)) == 0 && x && y, "bad arguments (m must be a power of two)");
     REQUIRE(wv == DB_HAAR || wv == DB_DB4, "unknown wavelet");
     REQUIRE(m >= make_filter(wv).kappa, "m smaller than the filter");
     cudaStream_t st = (cudaStream_t)stream;
@@ -906,7 +1767,7 @@ extern "C" db_status db_restrict(int m, db_wavelet wv, const void* x, void* y, d
 
 extern "C" db_status db_prolong(int mc, db_wavelet wv, const void* y, void* x, db_precision prec, db_stream stream) {
   return simple_call([&] {
-    REQUIRE(mc >= 1 && x && y, "bad arguments");
+    REQUIRE(mc >= 1 && (mc & (mc - 1)) == 0 && x && y, "bad arguments (mc must be a power of two)");
     REQUIRE(wv == DB_HAAR || wv == DB_DB4, "unknown wavelet");
     REQUIRE(2 * mc >= make_filter(wv).kappa, "m smaller than the filter");
     cudaStream_t st = (cudaStream_t)stream;
@@ -921,7 +1782,7 @@ extern "C" db_status db_prolong(int mc, db_wavelet wv, const void* y, void* x, d
 
 extern "C" db_status db_aux_prolong(int mc, db_wavelet wv, const void* qc, void* qf, db_precision prec, db_stream stream) {
   return simple_call([&] {
-    REQUIRE(mc >= 1 && qc && qf, "bad arguments");
+    REQUIRE(mc >= 1 && (mc & (mc - 1)) == 0 && qc && qf, "bad arguments (mc must be a power of two)");
     REQUIRE(wv == DB_HAAR || wv == DB_DB4, "unknown wavelet");
     REQUIRE(2 * mc >= make_filter(wv).kappa, "m smaller than the filter");
     cudaStream_t st = (cudaStream_t)stream;

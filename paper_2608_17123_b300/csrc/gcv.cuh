@@ -7,12 +7,12 @@
 //    K_k(A^T A, A^T b) (Lanczos on A^T A with two classical Gram-Schmidt
 //    passes per step) plus orth(D^T c) when the shift c is non-zero.
 //    G_A = V^T A^T A V, G_D = V^T D^T D V, g_A = V^T A^T b, g_D = V^T D^T c
-//    are accumulated as the basis grows (double). The pair is reduced to
-//    diagonal form Y^T G_A Y = diag(lam), Y^T (G_A + G_D) Y = I in double
-//    (Cholesky, congruence, Householder tridiagonalisation, implicit QR),
-//    after which the numerator is the sum of squares
-//      sum_j [gamma (sqrt(lam_j) d_j - ahat_j (1-lam_j)) / (lam_j + gamma(1-lam_j))]^2 + r0^2.
-//  * trace: the same pair under periodic boundary conditions,
+//    are accumulated as the basis grows (double) and the small problem is
+//    solved for each trial gamma in double (see k_gcv_select).
+//  * exact mode (levels with at most `exact_max_pixels` pixels): V = I, i.e.
+//    the dense matrices of the pair, and the exact trace -- the paper's
+//    definition.
+//  * trace (projected mode): the same pair under periodic boundary conditions,
 //      T(gamma) = sum_w 1 / (1 + gamma s rho_w),  rho_w = l(w) / |K(w)|^2,
 //    K = DFT of the level's interior stencil, l = 4 sin^2(pi j1/m) + 4 sin^2(pi j2/m),
 //    s = mean squared IRLS weight (1 for an unweighted pair).
@@ -139,9 +139,277 @@ __global__ void k_Lt_w(int m, const Acc* __restrict__ qx, const Acc* __restrict_
   }
 }
 
-// mean of w^2 over the valid gradient entries: sum via k_dot, divided on the host.
+// ---- fused Krylov-basis kernels ------------------------------------------------
+// Each block owns one contiguous chunk of the vectors; per-chunk partial sums
+// are kept as double-float pairs (float hi + float lo, error-free TwoSum) and
+// the block that finishes last adds the chunks in a fixed order.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float xh, float xl) {
+  const float s = hi + xh;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (xh - bp);
+  lo = lo + xl + e;
+  hi = s;
+}
+
+// Kahan-compensated warp dot over strided elements, returned as (hi, lo).
+__device__ __forceinline__ float2 warp_df(float acc, float comp) {
+  // combine acc (with Kahan residue -comp) across the warp
+  float hi = acc, lo = -comp;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    df_add(hi, lo, h2, l2);
+  }
+  return make_float2(hi, lo);
+}
+
+constexpr int VCH_E = 8;                 // elements per thread per chunk
+constexpr int VCH_THREADS = 256;
+constexpr int VCH_CHUNK = VCH_E * VCH_THREADS;
+enum VchunkMode { VCH_UPDATE = 1, VCH_DOTS = 2, VCH_NORM = 4 };
+
+// x -= sum_{i<nrows} coef[i*cstride] V_i (VCH_UPDATE); then V_i . x for
+// i < nrows into out[i*ostride] (VCH_DOTS) and/or x . x into *outnorm
+// (VCH_NORM). Float vectors only (the Krylov basis is held in working
+// precision); part needs (nrows + 1) * gridDim.x float2.
+__global__ void __launch_bounds__(VCH_THREADS) k_vchunk(size_t n, int nrows, const float* __restrict__ V, size_t ldv,
+    const double* __restrict__ coef, int cstride, float* __restrict__ x, int mode, float2* __restrict__ part,
+    unsigned* cnt, double* out, int ostride, double* outnorm, int E) {
+  __shared__ float xs[VCH_CHUNK];
+  __shared__ float cs[512];
+  __shared__ int s_last;
+  const int nch = gridDim.x, ch = blockIdx.x;
+  const int CH = E * VCH_THREADS;
+  const size_t beg = (size_t)ch * CH;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = VCH_THREADS / 32;
+  if (mode & VCH_UPDATE)
+    for (int i = tid; i < nrows; i += VCH_THREADS) cs[i] = (float)coef[(size_t)i * cstride];
+  __syncthreads();
+  float nacc = 0.f, ncomp = 0.f;
+  for (int k = 0; k < E; ++k) {
+    const int le = k * VCH_THREADS + tid;
+    const size_t e = beg + le;
+    float xv = 0.f;
+    if (e < n) {
+      xv = x[e];
+      if (mode & VCH_UPDATE) {
+        for (int i = 0; i < nrows; ++i) xv -= cs[i] * V[(size_t)i * ldv + e];
+        x[e] = xv;
+      }
+      const float y = xv * xv - ncomp;
+      const float t = nacc + y;
+      ncomp = (t - nacc) - y;
+      nacc = t;
+    }
+    xs[le] = xv;
+  }
+  __syncthreads();
+  if (mode & VCH_DOTS) {
+    for (int i = wid; i < nrows; i += nw) {
+      const float* vi = V + (size_t)i * ldv + beg;
+      float acc = 0.f, comp = 0.f;
+      for (int le = lane; le < CH; le += 32) {
+        if (beg + le >= n) break;
+        const float y = vi[le] * xs[le] - comp;
+        const float t = acc + y;
+        comp = (t - acc) - y;
+        acc = t;
+      }
+      const float2 r = warp_df(acc, comp);
+      if (lane == 0) part[(size_t)i * nch + ch] = r;
+    }
+  }
+  if (mode & VCH_NORM) {
+    const float2 r = warp_df(nacc, ncomp);
+    __shared__ float2 wn[8];
+    if (lane == 0) wn[wid] = r;
+    __syncthreads();
+    if (tid == 0) {
+      float hi = 0.f, lo = 0.f;
+      for (int w = 0; w < nw; ++w) df_add(hi, lo, wn[w].x, wn[w].y);
+      part[(size_t)nrows * nch + ch] = make_float2(hi, lo);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = (atomicAdd(cnt, 1u) == (unsigned)nch - 1);
+    __threadfence();
+  }
+  __syncthreads();
+  if (!s_last) return;
+  const int r0 = (mode & VCH_DOTS) ? 0 : nrows;
+  const int r1 = (mode & VCH_NORM) ? nrows + 1 : nrows;
+  for (int r = r0 + tid; r < r1; r += VCH_THREADS) {
+    float hi = 0.f, lo = 0.f;
+    for (int c = 0; c < nch; ++c) {
+      const float2 pv = __ldcg(&part[(size_t)r * nch + c]);
+      df_add(hi, lo, pv.x, pv.y);
+    }
+    const double v = (double)hi + (double)lo;
+    if (r < nrows) out[(size_t)r * ostride] = v; else *outnorm = v;
+  }
+  if (tid == 0) *cnt = 0;
+}
+
+// Gram column j: with y = L^T diag(w^2) L v_j (computed here),
+//   GA[i*ld + j] = V_i . t, GD[i*ld + j] = V_i . y (i <= j),
+//   gA[j] = atb . v_j, gD[j] = dtc . v_j (dtc may be null -> 0).
+template <typename T>
+__global__ void __launch_bounds__(VCH_THREADS) k_gram_col(int m, int j, const float* __restrict__ V,
+    const float* __restrict__ t, const T* __restrict__ wx, const T* __restrict__ wy, const float* __restrict__ atb,
+    const float* __restrict__ dtc, float2* __restrict__ part, unsigned* cnt, double* GA, double* GD, int ld,
+    double* gA, double* gD, int E) {
+  __shared__ float ts[VCH_CHUNK];
+  __shared__ float ys[VCH_CHUNK];
+  __shared__ int s_last;
+  const size_t n = (size_t)m * m;
+  const int nch = gridDim.x, ch = blockIdx.x;
+  const int CH = E * VCH_THREADS;
+  const size_t beg = (size_t)ch * CH;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = VCH_THREADS / 32;
+  const float* vj = V + (size_t)j * n;
+  for (int k = 0; k < E; ++k) {
+    const int le = k * VCH_THREADS + tid;
+    const size_t i = beg + le;
+    float tv = 0.f, yv = 0.f;
+    if (i < n) {
+      tv = t[i];
+      const int r = (int)(i % m), c = (int)(i / m);
+      const float xv = vj[i];
+      auto W = [&](const T* p, size_t q) -> float { return p ? (float)to_acc(p[q]) : 1.f; };
+      if (r < m - 1) { const float w = W(wx, i); yv -= w * w * (vj[i + 1] - xv); }
+      if (r > 0) { const float w = W(wx, i - 1); yv += w * w * (xv - vj[i - 1]); }
+      if (c < m - 1) { const float w = W(wy, i); yv -= w * w * (vj[i + m] - xv); }
+      if (c > 0) { const float w = W(wy, i - m); yv += w * w * (xv - vj[i - m]); }
+    }
+    ts[le] = tv;
+    ys[le] = yv;
+  }
+  __syncthreads();
+  const int nrows = j + 1;
+  // rows 0..j: two dots each (slots 2i, 2i+1); row j+1: atb.v_j and dtc.v_j
+  for (int i = wid; i <= nrows; i += nw) {
+    float a1 = 0.f, c1 = 0.f, a2 = 0.f, c2 = 0.f;
+    for (int le = lane; le < CH; le += 32) {
+      if (beg + le >= n) break;
+      float p1, q1, p2, q2;
+      if (i < nrows) { const float vv = V[(size_t)i * n + beg + le]; p1 = vv; q1 = ts[le]; p2 = vv; q2 = ys[le]; }
+      else { const float vv = vj[beg + le]; p1 = atb[beg + le]; q1 = vv; p2 = dtc ? dtc[beg + le] : 0.f; q2 = vv; }
+      float y = p1 * q1 - c1, tt = a1 + y; c1 = (tt - a1) - y; a1 = tt;
+      y = p2 * q2 - c2; tt = a2 + y; c2 = (tt - a2) - y; a2 = tt;
+    }
+    const float2 r1 = warp_df(a1, c1), r2 = warp_df(a2, c2);
+    if (lane == 0) {
+      part[(size_t)(2 * i) * nch + ch] = r1;
+      part[(size_t)(2 * i + 1) * nch + ch] = r2;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = (atomicAdd(cnt, 1u) == (unsigned)nch - 1);
+    __threadfence();
+  }
+  __syncthreads();
+  if (!s_last) return;
+  for (int sidx = tid; sidx < 2 * (nrows + 1); sidx += VCH_THREADS) {
+    float hi = 0.f, lo = 0.f;
+    for (int c = 0; c < nch; ++c) {
+      const float2 pv = __ldcg(&part[(size_t)sidx * nch + c]);
+      df_add(hi, lo, pv.x, pv.y);
+    }
+    const double v = (double)hi + (double)lo;
+    const int i = sidx >> 1;
+    if (i < nrows) {
+      if ((sidx & 1) == 0) GA[(size_t)i * ld + j] = v; else GD[(size_t)i * ld + j] = v;
+    } else {
+      if ((sidx & 1) == 0) gA[j] = v; else gD[j] = v;
+    }
+  }
+  if (tid == 0) *cnt = 0;
+}
+
+// ---- exact mode: dense matrices of the pair (n <= a few hundred) ------------
+// A[(r + c m), (r' + c' m)] = sum_t Cr_t[r, r'] Cc_t[c, c'], C[r, s] = B[r][(s - r - dlo) mod m].
+__device__ __forceinline__ double band_entry(const double* B, int t, int m, int dlo, int w, int r, int s) {
+  const int k = wrap(s - r - dlo, m);
+  return k < w ? B[((size_t)t * m + r) * w + k] : 0.0;
+}
+
+__global__ void k_dense_blur(int m, int nterms, int dlo, int w, const double* __restrict__ Br,
+                             const double* __restrict__ Bc, double* __restrict__ Ad) {
+  const int n = m * m;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)n * n;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int row = (int)(idx / n), col = (int)(idx % n);
+    const int r = row % m, c = row / m, r2 = col % m, c2 = col / m;
+    double v = 0.0;
+    for (int t = 0; t < nterms; ++t)
+      v += band_entry(Br, t, m, dlo, w, r, r2) * band_entry(Bc, t, m, dlo, w, c, c2);
+    Ad[idx] = v;
+  }
+}
+
+// G[i][j] = sum_l A[l][i] A[l][j]  (full n x n, row-major, leading dimension ld)
+__global__ void k_gram_dense(int n, const double* __restrict__ Ad, double* __restrict__ G, int ld) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)n * n;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    double s0 = 0.0, s1 = 0.0;
+    int l = 0;
+    for (; l + 1 < n; l += 2) { s0 += Ad[(size_t)l * n + i] * Ad[(size_t)l * n + j]; s1 += Ad[(size_t)(l + 1) * n + i] * Ad[(size_t)(l + 1) * n + j]; }
+    if (l < n) s0 += Ad[(size_t)l * n + i] * Ad[(size_t)l * n + j];
+    G[(size_t)i * ld + j] = s0 + s1;
+  }
+}
+
+// (L^T diag(w^2) L)[i][j] from the 5-point stencil (weights may be null).
+template <typename T>
+__global__ void k_dense_DtD(int m, const T* __restrict__ wx, const T* __restrict__ wy, double* __restrict__ G, int ld) {
+  const int n = m * m;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)n * n;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    const int r = i % m, c = i / m;
+    auto X = [&](int k) { return k == j ? 1.0 : 0.0; };
+    auto W = [&](const T* p, int k) { return p ? (double)to_acc(p[k]) : 1.0; };
+    double s = 0.0;
+    const double xv = X(i);
+    if (r < m - 1) { const double ww = W(wx, i); s -= ww * ww * (X(i + 1) - xv); }
+    if (r > 0) { const double ww = W(wx, i - 1); s += ww * ww * (xv - X(i - 1)); }
+    if (c < m - 1) { const double ww = W(wy, i); s -= ww * ww * (X(i + m) - xv); }
+    if (c > 0) { const double ww = W(wy, i - m); s += ww * ww * (xv - X(i - m)); }
+    G[(size_t)i * ld + j] = s;
+  }
+}
+
+// g = Ad^T b (Ad row-major n x n), double
+__global__ void k_dense_matvecT(int n, const double* __restrict__ Ad, const double* __restrict__ b, double* g) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) s += Ad[(size_t)l * n + j] * b[l];
+    g[j] = s;
+  }
+}
+
+template <typename Acc>
+__global__ void k_to_double(size_t n, const Acc* __restrict__ x, double* __restrict__ y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
 
 // ---- the small problem and the selection (one block) --------------------------
+// With M = G_A + G_D = R R^T (Cholesky), C = R^{-1} G_A R^{-T} = Q T Q^T
+// (Householder, T tridiagonal) and p_A = Q^T R^{-1} g_A, p_D = Q^T R^{-1} g_D,
+// the trial solution of (G_A + gamma G_D) y = g_A + gamma g_D is
+// y = R^{-T} Q w with ((1 - gamma) T + gamma I) w = p_A + gamma p_D (a
+// tridiagonal SPD system, one Thomas sweep per gamma); the residual is
+// evaluated without cancellation as gamma^2 u^T T u + r0^2 (sel_numerator).
+// The trace is either the symbol trace (projected mode) or, when the basis is
+// the whole space (exact mode, tiny levels), sum_j lam_j / (lam_j + gamma (1 - lam_j))
+// over the eigenvalues of T (bisection with Sturm counts).
 struct GcvSelectArgs {
   int kk;                 // basis dimension
   int ld;                 // leading dimension of GA, GD
@@ -152,15 +420,29 @@ struct GcvSelectArgs {
   double bnorm2;
   double n;               // pixel count of the level
   double s;               // weight scale of the trace
-  const float* rho;       // [npix] symbol ratios
+  const float* rho;       // [npix] symbol ratios (projected mode)
   int npix;
+  int exact;              // 1: trace from the eigenvalues of T
   double lo, hi, tolx;
   int npts, max_ext;
-  double* work;           // >= 3 kk*kk + 8 kk doubles
+  double* work;           // >= 3 kk*kk + (6 + 2*SEL_MAXPTS + 1) kk doubles
   double* out;            // out[0] = gamma, out[1] = extensions, out[2] = GCV value
 };
 
-constexpr int SEL_THREADS = 1024;
+constexpr int SEL_THREADS = 512;
+
+// 1/x in double from a float reciprocal refined by two Newton steps
+// (22 -> 44 -> 88 bits, i.e. correctly rounded to within an ulp); an FP64
+// divide costs several hundred cycles of latency on this part.
+__device__ __forceinline__ double rcp_d(double x) {
+  const double ax = fabs(x);
+  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / (ax > 1e-300 ? x : 1e-300);
+  double y = (double)__frcp_rn((float)x);
+  y = y * (2.0 - x * y);
+  y = y * (2.0 - x * y);
+  return y;
+}
+constexpr int SEL_MAXPTS = 64;
 
 __device__ double sel_block_sum(double v, double* sh) {
   v = warp_sum(v);
@@ -168,7 +450,7 @@ __device__ double sel_block_sum(double v, double* sh) {
   __syncthreads();
   if (lane == 0) sh[wid] = v;
   __syncthreads();
-  double s = (threadIdx.x < 32) ? sh[threadIdx.x] : 0.0;
+  double s = (threadIdx.x < 32 && threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
   if (threadIdx.x < 32) s = warp_sum(s);
   __syncthreads();
   if (threadIdx.x == 0) sh[0] = s;
@@ -178,50 +460,83 @@ __device__ double sel_block_sum(double v, double* sh) {
   return r;
 }
 
-// GCV at t = log10(gamma); all threads participate; returns the value in all.
-__device__ double sel_eval(const GcvSelectArgs& a, double t, const double* lam, const double* sl,
-                           const double* dd, const double* ahat, double r02, double* sh) {
-  const double gamma = pow(10.0, t);
-  // numerator: sum over the kk eigen-components
-  double e2 = 0.0;
-  for (int j = threadIdx.x; j < a.kk; j += blockDim.x) {
-    const double den = lam[j] + gamma * (1.0 - lam[j]);
-    const double e = gamma * (sl[j] * dd[j] - ahat[j] * (1.0 - lam[j])) / den;
-    e2 += e * e;
+// Solve ((1 - gamma) T + gamma I) u = f by one Thomas sweep (T symmetric
+// tridiagonal: diagonal d, off-diagonal e; the matrix is SPD for gamma > 0
+// and for gamma = 0 when T is). cw is scratch of length kk.
+__device__ void sel_tri_solve(int kk, const double* d, const double* e, const double* f, double gamma,
+                              double* cw, double* u, double shift = 0.0) {
+  const double a = 1.0 - gamma;
+  const double diag_add = gamma + shift;
+  double piv = a * d[0] + diag_add;
+  double inv = rcp_d(piv);
+  cw[0] = (kk > 1) ? (a * e[0]) * inv : 0.0;
+  u[0] = f[0] * inv;
+  for (int i = 1; i < kk; ++i) {
+    const double off = a * e[i - 1];
+    piv = a * d[i] + diag_add - off * cw[i - 1];
+    inv = rcp_d(piv);
+    cw[i] = (i + 1 < kk) ? (a * e[i]) * inv : 0.0;
+    u[i] = (f[i] - off * u[i - 1]) * inv;
   }
-  // trace: float terms, Kahan-compensated per thread, double across threads
-  const float gs = (float)(gamma * a.s);
-  float sum = 0.f, comp = 0.f;
-  for (int i = threadIdx.x; i < a.npix; i += blockDim.x) {
-    const float term = __frcp_rn(1.0f + gs * a.rho[i]);
-    const float y = term - comp;
-    const float tt = sum + y;
-    comp = (tt - sum) - y;
-    sum = tt;
+  for (int i = kk - 2; i >= 0; --i) u[i] -= cw[i] * u[i + 1];
+}
+
+// Numerator ||A V y_gamma - b||^2 = gamma^2 u^T T u + r0^2 with
+// ((1 - gamma) T + gamma I) u = f, f = p_A + p_D - T^{-1} p_A: the
+// gamma-dependent part is a quadratic form in T (no cancellation against
+// ||b||^2). One thread.
+__device__ double sel_numerator(int kk, const double* d, const double* e, const double* f, double r02,
+                                double gamma, double* cw, double* u) {
+  sel_tri_solve(kk, d, e, f, gamma, cw, u);
+  double q = 0.0;
+  for (int i = 0; i < kk; ++i) {
+    double tu = d[i] * u[i];
+    if (i > 0) tu += e[i - 1] * u[i - 1];
+    if (i + 1 < kk) tu += e[i] * u[i + 1];
+    q += u[i] * tu;
   }
-  double part[1];
-  const double num = sel_block_sum(e2, sh) + r02;
-  const double tr = sel_block_sum((double)sum - (double)comp, sh);
-  (void)part;
-  const double den = a.n - tr;
-  return num / (den * den);
+  return gamma * gamma * q + r02;
+}
+
+// Trace term for a set of gammas (all threads); returns per-gamma traces in tr[].
+__device__ void sel_traces(const GcvSelectArgs& a, const double* lam, int ng, const double* gam, double* tr,
+                           double* sh) {
+  for (int g = 0; g < ng; ++g) {
+    double part = 0.0;
+    if (a.exact) {
+      for (int j = threadIdx.x; j < a.kk; j += blockDim.x) {
+        const double l = lam[j];
+        part += l / (l + gam[g] * (1.0 - l));
+      }
+    } else {
+      const float gs = (float)(gam[g] * a.s);
+      float sum = 0.f, comp = 0.f;
+      for (int i = threadIdx.x; i < a.npix; i += blockDim.x) {
+        const float term = __frcp_rn(1.0f + gs * a.rho[i]);
+        const float y = term - comp;
+        const float t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+      }
+      part = (double)sum - (double)comp;
+    }
+    tr[g] = sel_block_sum(part, sh);
+  }
 }
 
 __global__ void __launch_bounds__(SEL_THREADS) k_gcv_select(GcvSelectArgs a) {
   __shared__ double sh[64];
-  __shared__ double s_val[4];
+  __shared__ double s_gam[SEL_MAXPTS], s_tr[SEL_MAXPTS], s_f[SEL_MAXPTS];
   const int kk = a.kk, ld = a.ld, tid = threadIdx.x, nth = blockDim.x;
   double* M = a.work;                 // kk x kk (row-major M[i*kk + j])
   double* C = M + kk * kk;            // kk x kk
   double* X = C + kk * kk;            // kk x kk
   double* pA = X + kk * kk;
   double* pD = pA + kk;
-  double* lam = pD + kk;
-  double* sl = lam + kk;
-  double* ahat = sl + kk;
-  double* dvec = ahat + kk;
-  double* ev = dvec + kk;             // tridiagonal diag
-  double* eo = ev + kk;               // tridiagonal off-diagonal
+  double* dg = pD + kk;               // tridiagonal diagonal
+  double* eo = dg + kk;               // tridiagonal off-diagonal
+  double* lam = eo + kk;              // eigenvalues of T (exact mode)
+  double* scratch = lam + 2 * kk;     // per-thread Thomas scratch for the grid: SEL_MAXPTS * 2 kk
   auto GAe = [&](int i, int j) { return i <= j ? a.GA[(size_t)i * ld + j] : a.GA[(size_t)j * ld + i]; };
   auto GDe = [&](int i, int j) { return i <= j ? a.GD[(size_t)i * ld + j] : a.GD[(size_t)j * ld + i]; };
   // 1. M = G_A + G_D, C = G_A (full symmetric)
@@ -231,42 +546,69 @@ __global__ void __launch_bounds__(SEL_THREADS) k_gcv_select(GcvSelectArgs a) {
     C[idx] = GAe(i, j);
   }
   __syncthreads();
-  double maxdiag = 0.0;
-  for (int i = 0; i < kk; ++i) maxdiag = fmax(maxdiag, M[i * kk + i]);
-  // 2. Cholesky M = R R^T (lower, in place)
+  __shared__ double s_md;
+  if (tid == 0) {
+    double md = 0.0;
+    for (int i = 0; i < kk; ++i) md = fmax(md, M[i * kk + i]);
+    s_md = md;
+  }
+  __syncthreads();
+  const double md = s_md;
+  const double piv_floor = 1e-14 * md;
+  // 2. Cholesky M = R R^T (lower, in place); rdiag = 1 / diag(R)
+  double* rdiag = lam + kk;           // kk entries before the Thomas scratch
+  __shared__ double s_rc;
   for (int c = 0; c < kk; ++c) {
     if (tid == 0) {
-      double piv = M[c * kk + c];
-      double floor_ = 1e-14 * maxdiag;
-      M[c * kk + c] = sqrt(piv > floor_ ? piv : floor_);
+      const double piv = M[c * kk + c];
+      const double r = sqrt(piv > piv_floor ? piv : piv_floor);
+      M[c * kk + c] = r;
+      s_rc = 1.0 / r;
+      rdiag[c] = s_rc;
     }
     __syncthreads();
-    const double rc = M[c * kk + c];
-    for (int i = c + 1 + tid; i < kk; i += nth) M[i * kk + c] /= rc;
+    const double rc = s_rc;
+    for (int i = c + 1 + tid; i < kk; i += nth) M[i * kk + c] *= rc;
     __syncthreads();
     const int rem = kk - c - 1;
     for (int idx = tid; idx < rem * rem; idx += nth) {
-      int i = c + 1 + idx / rem, j = c + 1 + idx % rem;
+      const int i = c + 1 + idx / rem, j = c + 1 + idx % rem;
       if (j <= i) M[i * kk + j] -= M[i * kk + c] * M[j * kk + c];
     }
     __syncthreads();
   }
-  // 3. X = R^{-1} G_A (column by column), pA = R^{-1} g_A, pD = R^{-1} g_D
+  // 3. X = R^{-1} G_A, pA = R^{-1} g_A, pD = R^{-1} g_D (one column per thread,
+  //    four partial sums to shorten the dependent chain)
   for (int q = tid; q < kk + 2; q += nth) {
     for (int i = 0; i < kk; ++i) {
-      double s = q < kk ? C[i * kk + q] : (q == kk ? a.gA[i] : a.gD[i]);
-      for (int l = 0; l < i; ++l) s -= M[i * kk + l] * (q < kk ? X[l * kk + q] : (q == kk ? pA[l] : pD[l]));
-      s /= M[i * kk + i];
-      if (q < kk) X[i * kk + q] = s; else if (q == kk) pA[i] = s; else pD[i] = s;
+      double s0 = q < kk ? C[i * kk + q] : (q == kk ? a.gA[i] : a.gD[i]);
+      double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int l = 0;
+      for (; l + 3 < i; l += 4) {
+        const double x0 = q < kk ? X[l * kk + q] : (q == kk ? pA[l] : pD[l]);
+        const double x1 = q < kk ? X[(l + 1) * kk + q] : (q == kk ? pA[l + 1] : pD[l + 1]);
+        const double x2 = q < kk ? X[(l + 2) * kk + q] : (q == kk ? pA[l + 2] : pD[l + 2]);
+        const double x3 = q < kk ? X[(l + 3) * kk + q] : (q == kk ? pA[l + 3] : pD[l + 3]);
+        s0 -= M[i * kk + l] * x0; s1 -= M[i * kk + l + 1] * x1;
+        s2 -= M[i * kk + l + 2] * x2; s3 -= M[i * kk + l + 3] * x3;
+      }
+      for (; l < i; ++l) s0 -= M[i * kk + l] * (q < kk ? X[l * kk + q] : (q == kk ? pA[l] : pD[l]));
+      const double v = ((s0 + s1) + (s2 + s3)) * rdiag[i];
+      if (q < kk) X[i * kk + q] = v; else if (q == kk) pA[i] = v; else pD[i] = v;
     }
   }
   __syncthreads();
   // 4. C = R^{-1} X^T  (= R^{-1} G_A R^{-T})
   for (int q = tid; q < kk; q += nth) {
     for (int i = 0; i < kk; ++i) {
-      double s = X[q * kk + i];
-      for (int l = 0; l < i; ++l) s -= M[i * kk + l] * C[l * kk + q];
-      C[i * kk + q] = s / M[i * kk + i];
+      double s0 = X[q * kk + i], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int l = 0;
+      for (; l + 3 < i; l += 4) {
+        s0 -= M[i * kk + l] * C[l * kk + q]; s1 -= M[i * kk + l + 1] * C[(l + 1) * kk + q];
+        s2 -= M[i * kk + l + 2] * C[(l + 2) * kk + q]; s3 -= M[i * kk + l + 3] * C[(l + 3) * kk + q];
+      }
+      for (; l < i; ++l) s0 -= M[i * kk + l] * C[l * kk + q];
+      C[i * kk + q] = ((s0 + s1) + (s2 + s3)) * rdiag[i];
     }
   }
   __syncthreads();
@@ -284,132 +626,144 @@ __global__ void __launch_bounds__(SEL_THREADS) k_gcv_select(GcvSelectArgs a) {
     for (int i = tid; i < len; i += nth) { double xv = C[(k + 1 + i) * kk + k]; part += xv * xv; }
     const double nx2 = sel_block_sum(part, sh);
     const double x0 = C[(k + 1) * kk + k];
-    const double nx = sqrt(nx2);
-    if (nx2 - x0 * x0 <= 1e-300 * (1.0 + nx2)) {   // already tridiagonal in this column
-      __syncthreads();
-      continue;
+    if (nx2 - x0 * x0 <= 1e-300 * (1.0 + nx2)) continue;   // column already reduced
+    // u = (x - alpha e1) / ||x - alpha e1||, ||x - alpha e1||^2 = 2 nx (nx + |x0|)
+    __shared__ double s_alpha, s_inu;
+    if (tid == 0) {
+      const double nx = sqrt(nx2);
+      s_alpha = x0 >= 0 ? -nx : nx;
+      s_inu = 1.0 / sqrt(2.0 * nx * (nx + fabs(x0)));
     }
-    const double alpha = x0 >= 0 ? -nx : nx;
-    // u = x - alpha e1, normalised
-    for (int i = tid; i < len; i += nth) u[i] = C[(k + 1 + i) * kk + k] - (i == 0 ? alpha : 0.0);
     __syncthreads();
-    double pu = 0.0;
-    for (int i = tid; i < len; i += nth) pu += u[i] * u[i];
-    const double nu = sqrt(sel_block_sum(pu, sh));
-    for (int i = tid; i < len; i += nth) u[i] /= nu;
+    const double alpha = s_alpha, inv_nu = s_inu;
+    for (int i = tid; i < len; i += nth) u[i] = (C[(k + 1 + i) * kk + k] - (i == 0 ? alpha : 0.0)) * inv_nu;
     __syncthreads();
-    // p = C22 u
     for (int i = tid; i < len; i += nth) {
-      double s = 0.0;
-      for (int j = 0; j < len; ++j) s += C[(k + 1 + i) * kk + (k + 1 + j)] * u[j];
-      p[i] = s;
+      const double* row = C + (size_t)(k + 1 + i) * kk + (k + 1);
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int j = 0;
+      for (; j + 3 < len; j += 4) { s0 += row[j] * u[j]; s1 += row[j + 1] * u[j + 1]; s2 += row[j + 2] * u[j + 2]; s3 += row[j + 3] * u[j + 3]; }
+      for (; j < len; ++j) s0 += row[j] * u[j];
+      p[i] = (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
-    double pk = 0.0;
-    for (int i = tid; i < len; i += nth) pk += u[i] * p[i];
+    double pk = 0.0, da = 0.0, dd = 0.0;
+    for (int i = tid; i < len; i += nth) { pk += u[i] * p[i]; da += u[i] * pA[k + 1 + i]; dd += u[i] * pD[k + 1 + i]; }
     const double K = sel_block_sum(pk, sh);
-    // w = 2p - 2K u ; C22 -= u w^T + w u^T
+    da = sel_block_sum(da, sh);
+    dd = sel_block_sum(dd, sh);
     for (int idx = tid; idx < len * len; idx += nth) {
-      int i = idx / len, j = idx % len;
+      const int i = idx / len, j = idx % len;
       const double wi = 2.0 * p[i] - 2.0 * K * u[i], wj = 2.0 * p[j] - 2.0 * K * u[j];
       C[(k + 1 + i) * kk + (k + 1 + j)] -= u[i] * wj + wi * u[j];
     }
-    // column / row k
     for (int i = tid; i < len; i += nth) {
       const double v = (i == 0) ? alpha : 0.0;
       C[(k + 1 + i) * kk + k] = v;
       C[k * kk + (k + 1 + i)] = v;
+      pA[k + 1 + i] -= 2.0 * da * u[i];
+      pD[k + 1 + i] -= 2.0 * dd * u[i];
     }
-    // reflect pA, pD
-    double da = 0.0, dd = 0.0;
-    for (int i = tid; i < len; i += nth) { da += u[i] * pA[k + 1 + i]; dd += u[i] * pD[k + 1 + i]; }
-    da = sel_block_sum(da, sh);
-    dd = sel_block_sum(dd, sh);
-    for (int i = tid; i < len; i += nth) { pA[k + 1 + i] -= 2.0 * da * u[i]; pD[k + 1 + i] -= 2.0 * dd * u[i]; }
     __syncthreads();
   }
   for (int i = tid; i < kk; i += nth) {
-    ev[i] = C[i * kk + i];
+    dg[i] = C[i * kk + i];
     eo[i] = (i + 1 < kk) ? C[(i + 1) * kk + i] : 0.0;
   }
   __syncthreads();
-  // 6. implicit symmetric QR with Wilkinson shifts on (ev, eo); rotations applied to pA, pD.
+  // 5b. w0 = T^{-1} p_A, f = p_A + p_D - w0, r0^2 = ||b||^2 - p_A . w0
+  double* fvec = scratch + (size_t)SEL_MAXPTS * 2 * kk;     // kk
+  __shared__ double s_r02;
   if (tid == 0) {
-    int hi = kk - 1;
-    int guard = 0;
-    while (hi > 0 && guard < 60 * kk) {
-      ++guard;
-      // deflate
-      if (fabs(eo[hi - 1]) <= 1e-15 * (fabs(ev[hi - 1]) + fabs(ev[hi]))) { eo[hi - 1] = 0.0; --hi; continue; }
-      int lo = hi - 1;
-      while (lo > 0 && fabs(eo[lo - 1]) > 1e-15 * (fabs(ev[lo - 1]) + fabs(ev[lo]))) --lo;
-      // Wilkinson shift from the trailing 2x2
-      const double dlt = 0.5 * (ev[hi - 1] - ev[hi]);
-      const double b2 = eo[hi - 1] * eo[hi - 1];
-      const double sgn = dlt >= 0 ? 1.0 : -1.0;
-      const double mu = ev[hi] - b2 / (dlt + sgn * sqrt(dlt * dlt + b2));
-      double xq = ev[lo] - mu, zq = eo[lo];
-      for (int k = lo; k < hi; ++k) {
-        // Givens rotation zeroing zq against xq
-        double c, s;
-        if (zq == 0.0) { c = 1.0; s = 0.0; }
-        else if (fabs(zq) > fabs(xq)) { double tau = -xq / zq; s = 1.0 / sqrt(1.0 + tau * tau); c = s * tau; }
-        else { double tau = -zq / xq; c = 1.0 / sqrt(1.0 + tau * tau); s = c * tau; }
-        // T <- G^T T G on rows/cols k, k+1 (G = [c s; -s c])
-        if (k > lo) eo[k - 1] = c * eo[k - 1] - s * zq;
-        const double a11 = ev[k], a22 = ev[k + 1], a12 = eo[k];
-        ev[k] = c * c * a11 - 2.0 * c * s * a12 + s * s * a22;
-        ev[k + 1] = s * s * a11 + 2.0 * c * s * a12 + c * c * a22;
-        eo[k] = c * s * (a11 - a22) + (c * c - s * s) * a12;
-        if (k + 1 < hi) { xq = eo[k]; zq = -s * eo[k + 1]; eo[k + 1] = c * eo[k + 1]; }
-        // accumulate: vectors in the eigenbasis, v <- G^T v
-        const double ya = pA[k], za = pA[k + 1];
-        pA[k] = c * ya - s * za; pA[k + 1] = s * ya + c * za;
-        const double yd = pD[k], zd = pD[k + 1];
-        pD[k] = c * yd - s * zd; pD[k + 1] = s * yd + c * zd;
-      }
+    double* w0 = scratch;
+    sel_tri_solve(kk, dg, eo, pA, 0.0, scratch + kk, w0, 0.0);
+    double pw = 0.0;
+    for (int i = 0; i < kk; ++i) {
+      pw += pA[i] * w0[i];
+      fvec[i] = pA[i] + pD[i] - w0[i];
     }
+    const double r = a.bnorm2 - pw;
+    s_r02 = r > 0.0 ? r : 0.0;
   }
   __syncthreads();
-  // 7. diagonal form
-  for (int j = tid; j < kk; j += nth) {
-    double l = ev[j];
-    l = l < 0.0 ? 0.0 : (l > 1.0 ? 1.0 : l);
-    lam[j] = l;
-    sl[j] = sqrt(l);
-    ahat[j] = l > 0.0 ? pA[j] / sqrt(l) : 0.0;
-    dvec[j] = pD[j];
+  const double r02 = s_r02;
+  // 6. exact mode: eigenvalues of T by bisection (Sturm counts), one per thread
+  if (a.exact) {
+    double glo = 0.0, ghi = 0.0;
+    for (int i = 0; i < kk; ++i) {   // Gershgorin interval
+      const double r = (i > 0 ? fabs(eo[i - 1]) : 0.0) + (i + 1 < kk ? fabs(eo[i]) : 0.0);
+      glo = fmin(glo, dg[i] - r);
+      ghi = fmax(ghi, dg[i] + r);
+    }
+    for (int j = tid; j < kk; j += nth) {
+      double l = glo, h = ghi;
+      for (int it = 0; it < 64; ++it) {
+        const double x = 0.5 * (l + h);
+        int cnt = 0;
+        double q = dg[0] - x;
+        if (q < 0) ++cnt;
+        for (int i = 1; i < kk; ++i) {
+          const double qq = (q != 0.0) ? q : 1e-300;
+          q = dg[i] - x - eo[i - 1] * eo[i - 1] / qq;
+          if (q < 0) ++cnt;
+        }
+        if (cnt > j) h = x; else l = x;   // cnt = number of eigenvalues below x
+      }
+      double v = 0.5 * (l + h);
+      lam[j] = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  double pr = 0.0;
-  for (int j = tid; j < kk; j += nth) pr += ahat[j] * ahat[j];
-  double r02 = a.bnorm2 - sel_block_sum(pr, sh);
-  r02 = r02 > 0.0 ? r02 : 0.0;
-  // 8. grid search (+ widening) and Brent refinement on t = log10(gamma)
+  // 7. grid search (parallel over the grid points) with widening, then Brent
+  const int npts = a.npts < SEL_MAXPTS ? a.npts : SEL_MAXPTS;
   double lo = a.lo, hi = a.hi;
   int ext = 0, jbest = 0;
   double fbest = 0.0, step = 0.0;
   for (;;) {
-    step = (hi - lo) / (a.npts - 1);
-    jbest = 0;
-    fbest = 0.0;
-    for (int j = 0; j < a.npts; ++j) {
-      const double t = (j == a.npts - 1) ? hi : lo + j * step;
-      const double f = sel_eval(a, t, lam, sl, dvec, ahat, r02, sh);
-      if (j == 0 || f < fbest) { fbest = f; jbest = j; }
+    step = (hi - lo) / (npts - 1);
+    for (int j = tid; j < npts; j += nth) s_gam[j] = pow(10.0, (j == npts - 1) ? hi : lo + j * step);
+    __syncthreads();
+    sel_traces(a, lam, npts, s_gam, s_tr, sh);
+    for (int j = tid; j < npts; j += nth) {
+      const double num = sel_numerator(kk, dg, eo, fvec, r02, s_gam[j], scratch + (size_t)j * 2 * kk,
+                                       scratch + (size_t)j * 2 * kk + kk);
+      const double den = a.n - s_tr[j];
+      s_f[j] = num / (den * den);
     }
+    __syncthreads();
+    jbest = 0;
+    fbest = s_f[0];
+    for (int j = 1; j < npts; ++j)
+      if (s_f[j] < fbest) { fbest = s_f[j]; jbest = j; }
+    __syncthreads();
     if (jbest == 0 && ext < a.max_ext) { lo -= 4.0; ++ext; continue; }
-    if (jbest == a.npts - 1 && ext < a.max_ext) { hi += 4.0; ++ext; continue; }
+    if (jbest == npts - 1 && ext < a.max_ext) { hi += 4.0; ++ext; continue; }
     break;
   }
-  auto tgrid = [&](int j) { return (j == a.npts - 1) ? hi : lo + j * step; };
+  auto tgrid = [&](int j) { return (j == npts - 1) ? hi : lo + j * step; };
+  auto feval = [&](double t) -> double {
+    __syncthreads();
+    if (tid == 0) s_gam[0] = pow(10.0, t);
+    __syncthreads();
+    sel_traces(a, lam, 1, s_gam, s_tr, sh);
+    if (tid == 0) {
+      const double num = sel_numerator(kk, dg, eo, fvec, r02, s_gam[0], scratch, scratch + kk);
+      const double den = a.n - s_tr[0];
+      s_f[0] = num / (den * den);
+    }
+    __syncthreads();
+    const double f = s_f[0];
+    __syncthreads();
+    return f;
+  };
   double A = tgrid(jbest > 0 ? jbest - 1 : 0);
-  double B = tgrid(jbest < a.npts - 1 ? jbest + 1 : a.npts - 1);
-  // Brent (all threads run the same control flow; values are identical)
+  double B = tgrid(jbest < npts - 1 ? jbest + 1 : npts - 1);
+  // Brent (golden section + parabolic interpolation); every thread runs the
+  // same control flow on the same broadcast values.
   const double cgold = 0.5 * (3.0 - sqrt(5.0));
   const double sqeps = sqrt(2.220446049250313e-16);
   double x = A + cgold * (B - A), w = x, v = x;
-  double fx = sel_eval(a, x, lam, sl, dvec, ahat, r02, sh), fw = fx, fv = fx;
+  double fx = feval(x), fw = fx, fv = fx;
   double d = 0.0, e = 0.0;
   for (int nfev = 1; nfev < 500; ++nfev) {
     const double xm = 0.5 * (A + B);
@@ -435,7 +789,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_gcv_select(GcvSelectArgs a) {
     }
     if (golden) { e = (x < xm) ? (B - x) : (A - x); d = cgold * e; }
     const double uu = (fabs(d) >= tol1) ? x + d : x + (d > 0 ? tol1 : -tol1);
-    const double fu = sel_eval(a, uu, lam, sl, dvec, ahat, r02, sh);
+    const double fu = feval(uu);
     if (fu <= fx) {
       if (uu < x) B = x; else A = x;
       v = w; fv = fw; w = x; fw = fx; x = uu; fx = fu;
@@ -451,7 +805,6 @@ __global__ void __launch_bounds__(SEL_THREADS) k_gcv_select(GcvSelectArgs a) {
     a.out[1] = (double)ext;
     a.out[2] = (fx <= fbest) ? fx : fbest;
   }
-  (void)s_val;
 }
 
 }  // namespace db

@@ -25,6 +25,7 @@ struct LsqrProb {
   BandOp<Acc> op;
   int m, solver;                 // 0 IRLS (weighted D), 1 MM (c = a0), 2 SB (c = a0 - a1)
   double gamma;
+  Acc sg;                        // sqrt(gamma) in working precision
   const T* b;
   const T* x0;                   // null: start from zero
   const T *a0x, *a0y, *a1x, *a1y;
@@ -34,8 +35,18 @@ struct LsqrProb {
 
 struct LsqrState {
   double alpha, beta, rhobar, phibar, anorm2, dnorm2, bnorm;
-  double phi_rho, theta_rho, rho_last, t_rnorm, t_arnorm;
+  double phi_rho, theta_rho, irho_last, t_rnorm, t_arnorm;
   int it, done, its, stop;       // stop: 1 S1, 2 S2, 3 S3, 4 maxit, 5 zero rhs/A^T rhs
+};
+
+// Working-precision coefficients of the next pass, written once per problem
+// by the block that finished the previous pass (so no thread repeats the
+// double-precision divisions):
+//   pass F: v = v~ * inv_alpha, u~_new = A_hat v - ab * u~, delta += phr w, w = v - thr w
+//   pass B: u = u~ * inv_beta, v~_new = A_hat^T u - ba * v~
+template <typename Acc>
+struct LsqrCoef {
+  Acc inv_alpha, ab, phr, thr, inv_beta, ba;
 };
 
 struct LsqrCtl {
@@ -45,30 +56,13 @@ struct LsqrCtl {
   double* part;                  // [ntiles * 3] per-tile partial sums
   unsigned* cnt;                 // [nprob] tiles finished in the current phase
   LsqrState* st;                 // [nprob]
+  void* coef;                    // [nprob] LsqrCoef<Acc>
   GridBarrier* gb;
   unsigned long long limit_ns;
 };
 
-template <typename T> __device__ __forceinline__ typename Traits<T>::Acc ldcg(const T* p);
-template <> __device__ __forceinline__ float ldcg<float>(const float* p) { return __ldcg(p); }
-template <> __device__ __forceinline__ double ldcg<double>(const double* p) { return __ldcg(p); }
-template <> __device__ __forceinline__ float ldcg<__nv_bfloat16>(const __nv_bfloat16* p) {
-  unsigned short u = __ldcg(reinterpret_cast<const unsigned short*>(p));
-  return __bfloat162float(__ushort_as_bfloat16(u));
-}
-
-// Same as load_tile but bypassing L1 (data written earlier in this launch).
-template <typename T, typename Acc>
-__device__ __forceinline__ void load_tile_cg(const T* X, int m, int r0, int c0, const TileGeom& g,
-                                             Acc scale, Acc* sx) {
-  const int tid = threadIdx.x + 32 * threadIdx.y;
-  const int H = g.H;
-  for (int idx = tid; idx < H * H; idx += 32 * TY) {
-    int cc = idx / H, rr = idx - cc * H;
-    int gr = wrap(r0 + g.lo + rr, m), gc = wrap(c0 + g.lo + cc, m);
-    sx[idx] = (Acc)ldcg<T>(X + gr + (size_t)gc * m) * scale;
-  }
-}
+template <typename T>
+__device__ __forceinline__ typename Traits<T>::Acc ldcg(const T* p) { return gload<true, T>(p); }
 
 __device__ __forceinline__ LsqrState load_state(const LsqrState* s) {
   LsqrState r;
@@ -83,41 +77,35 @@ __device__ __forceinline__ LsqrState load_state(const LsqrState* s) {
   return r;
 }
 
-// Reduce this tile's NV partials; returns true in the block that completed the
-// last tile of problem p (and has to finish the problem's reduction).
-template <int NV>
-__device__ __forceinline__ bool finish_tile(double (&red)[NV], double* part, unsigned* cnt, int tile,
-                                            int p, int ntiles_p, double* scratch, int* s_flag) {
-  block_sum<NV>(red, scratch);
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) part[(size_t)tile * NV + k] = red[k];
-    __threadfence();
-    unsigned old = atomicAdd(&cnt[p], 1u);
-    *s_flag = (old == (unsigned)ntiles_p - 1);
-    __threadfence();
-  }
-  __syncthreads();
-  return *s_flag != 0;
+// Loads of one tile issued before any of them is used: the problem's done
+// flag and coefficients, the pointwise operands of this thread's pixels, the
+// (unscaled) input window and the band rows of term 0. A pass then waits on
+// a single memory round trip instead of a chain of them. The scale of the
+// input (1/alpha or 1/beta) is applied to the outputs, which are linear in it.
+template <typename Acc>
+struct TileHead {
+  int done;
+  LsqrCoef<Acc> K;
+};
+
+template <typename Acc>
+__device__ __forceinline__ TileHead<Acc> load_head(const LsqrCtl& ctl, int p) {
+  TileHead<Acc> h;
+  h.done = __ldcg(&ctl.st[p].done);
+  const Acc* kc = reinterpret_cast<const Acc*>(reinterpret_cast<const LsqrCoef<Acc>*>(ctl.coef) + p);
+  h.K.inv_alpha = __ldcg(kc + 0);
+  h.K.ab = __ldcg(kc + 1);
+  h.K.phr = __ldcg(kc + 2);
+  h.K.thr = __ldcg(kc + 3);
+  h.K.inv_beta = __ldcg(kc + 4);
+  h.K.ba = __ldcg(kc + 5);
+  return h;
 }
 
-// Fixed-order sum of a problem's tile partials by warp 0 (result in lane 0).
-template <int NV>
-__device__ __forceinline__ void problem_sum(const double* part, int tile_begin, int ntiles, double (&out)[NV]) {
-  const int lane = threadIdx.x;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) out[k] = 0.0;
-  for (int t = lane; t < ntiles; t += 32) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) out[k] += __ldcg(part + (size_t)(tile_begin + t) * NV + k);
-  }
-#pragma unroll
-  for (int k = 0; k < NV; ++k) out[k] = warp_sum(out[k]);
-}
-
+// Returns false (nothing written) when the problem has already stopped.
 template <typename T, typename Acc>
-__device__ void lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrState& S, bool init, bool first,
-                            int r0, int c0, Acc* sm, double (&red)[3]) {
+__device__ bool lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p, bool init, bool first,
+                            int r0, int c0, Acc* sm, Acc (&red)[3]) {
   const int m = P.m;
   const TileGeom g = tile_geom(P.op, false);
   Acc* sx = sm;
@@ -125,16 +113,39 @@ __device__ void lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrState& S, bool 
   Acc* sbr = sz + g.H * TM;
   Acc* sbc = sbr + TM * band_pitch(g.w);
   const T* src = init ? P.x0 : P.v;
-  const Acc inv_alpha = init ? Acc(1) : (S.alpha > 0.0 ? (Acc)(1.0 / S.alpha) : Acc(0));
-  Acc Av[PIX] = {};
-  __syncthreads();
-  if (src) {
-    load_tile_cg<T, Acc>(src, m, r0, c0, g, inv_alpha, sx);
-    tile_conv<Acc>(P.op, false, r0, c0, g, sx, sz, sbr, sbc, Av);
+  const TileHead<Acc> h = load_head<Acc>(ctl, p);
+  const bool wtd = (P.solver == 0);
+  Acc pu[PIX], px[PIX], py[PIX], pw_[PIX], pd[PIX], wx[PIX], wy[PIX];
+  {
+    const int rr = r0 + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < PIX; ++j) {
+      const int cc = c0 + threadIdx.y + TY * j;
+      pu[j] = px[j] = py[j] = pw_[j] = pd[j] = Acc(0);
+      wx[j] = wy[j] = Acc(1);
+      if (rr < m && cc < m) {
+        const size_t i = rr + (size_t)cc * m;
+        if (!init) {
+          pu[j] = ldcg<T>(P.uA + i);
+          px[j] = ldcg<T>(P.uLx + i);
+          py[j] = ldcg<T>(P.uLy + i);
+          if (!first) { pw_[j] = ldcg<T>(P.w + i); pd[j] = ldcg<T>(P.dlt + i); }
+        }
+        if (wtd) { wx[j] = to_acc(P.a0x[i]); wy[j] = to_acc(P.a0y[i]); }
+      }
+    }
   }
-  const Acc sg = (Acc)sqrt(P.gamma);
-  const Acc ab = (!init && S.beta > 0.0) ? (Acc)(S.alpha / S.beta) : Acc(0);
-  const Acc phr = (Acc)S.phi_rho, thr = (Acc)S.theta_rho;
+  if (src) {
+    gather_tile<true, T, Acc>(src, m, r0, c0, g, Acc(1), sx);
+    load_bands<Acc>(P.op, false, 0, r0, c0, g, sbr, sbc);
+  }
+  if (h.done) return false;
+  Acc Av[PIX] = {};
+  if (src) tile_conv<Acc>(P.op, false, r0, c0, g, sx, sz, sbr, sbc, Av, true);
+  const Acc sc = init ? Acc(1) : h.K.inv_alpha;   // v = v~ / alpha
+  const Acc sg = P.sg;
+  const Acc ab = init ? Acc(0) : h.K.ab;
+  const Acc phr = h.K.phr, thr = h.K.thr;
   const int r = r0 + threadIdx.x;
   const int lr = threadIdx.x - g.lo;
   Acc s_u = 0, s_d = 0, s_w = 0;
@@ -147,29 +158,32 @@ __device__ void lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrState& S, bool 
     const int lc = cl - g.lo;
     Acc v0 = 0, qx = 0, qy = 0;
     if (src) {
-      v0 = sx[lc * g.H + lr];
-      if (r < m - 1) qx = sx[lc * g.H + lr + 1] - v0;
-      if (c < m - 1) qy = sx[(lc + 1) * g.H + lr] - v0;
+      const Acc x0 = sx[lc * g.H + lr];
+      v0 = sc * x0;
+      if (r < m - 1) qx = sc * (sx[lc * g.H + lr + 1] - x0);
+      if (c < m - 1) qy = sc * (sx[(lc + 1) * g.H + lr] - x0);
     }
-    if (P.solver == 0) { qx *= to_acc(P.a0x[i]); qy *= to_acc(P.a0y[i]); }
+    qx *= wx[j];
+    qy *= wy[j];
+    const Acc av = sc * Av[j];
     Acc ua, ux, uy;
     if (init) {
       Acc cx = 0, cy = 0;
       if (P.solver == 1) { cx = to_acc(P.a0x[i]); cy = to_acc(P.a0y[i]); }
       else if (P.solver == 2) { cx = to_acc(P.a0x[i]) - to_acc(P.a1x[i]); cy = to_acc(P.a0y[i]) - to_acc(P.a1y[i]); }
-      ua = to_acc(P.b[i]) - Av[j];
+      ua = to_acc(P.b[i]) - av;
       ux = sg * (cx - qx);
       uy = sg * (cy - qy);
       P.dlt[i] = store_cast<T, Acc>(Acc(0));
     } else {
-      ua = Av[j] - ab * ldcg<T>(P.uA + i);
-      ux = sg * qx - ab * ldcg<T>(P.uLx + i);
-      uy = sg * qy - ab * ldcg<T>(P.uLy + i);
+      ua = av - ab * pu[j];
+      ux = sg * qx - ab * px[j];
+      uy = sg * qy - ab * py[j];
       if (first) {
         P.w[i] = store_cast<T, Acc>(v0);
       } else {
-        const Acc wo = ldcg<T>(P.w + i);
-        const Acc dn = ldcg<T>(P.dlt + i) + phr * wo;
+        const Acc wo = pw_[j];
+        const Acc dn = pd[j] + phr * wo;
         P.dlt[i] = store_cast<T, Acc>(dn);
         P.w[i] = store_cast<T, Acc>(v0 - thr * wo);
         s_d += dn * dn;
@@ -183,55 +197,87 @@ __device__ void lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrState& S, bool 
     P.uLy[i] = store_cast<T, Acc>(uy);
     s_u += ua * ua + ux * ux + uy * uy;
   }
-  red[0] = (double)s_u;
-  red[1] = (double)s_d;
-  red[2] = (double)s_w;
+  red[0] = s_u;
+  red[1] = s_d;
+  red[2] = s_w;
+  return true;
 }
 
 template <typename T, typename Acc>
-__device__ void lsqr_pass_B(const LsqrProb<T, Acc>& P, const LsqrState& S, bool init,
-                            int r0, int c0, Acc* sm, double (&red)[3]) {
+__device__ bool lsqr_pass_B(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p, bool init,
+                            int r0, int c0, Acc* sm, Acc (&red)[3]) {
   const int m = P.m;
   const TileGeom g = tile_geom(P.op, true);
   Acc* sx = sm;
   Acc* sz = sx + g.H * g.H;
   Acc* sbr = sz + g.H * TM;
   Acc* sbc = sbr + TM * band_pitch(g.w);
-  const Acc inv_beta = S.beta > 0.0 ? (Acc)(1.0 / S.beta) : Acc(0);
+  const TileHead<Acc> h = load_head<Acc>(ctl, p);
+  const bool wtd = (P.solver == 0);
+  // L^T applied to the (unscaled) gradient planes of this thread's pixels, and the old v
+  Acc lt[PIX], vo[PIX];
+  {
+    const int rr = r0 + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < PIX; ++j) {
+      const int cc = c0 + threadIdx.y + TY * j;
+      Acc l = 0, v = 0;
+      if (rr < m && cc < m) {
+        // all loads issued unconditionally (clamped neighbours), then combined
+        const size_t i = rr + (size_t)cc * m;
+        const bool dn = rr < m - 1, up = rr > 0, rt = cc < m - 1, lf = cc > 0;
+        const size_t iu = up ? i - 1 : i, il = lf ? i - m : i;
+        const Acc x0 = ldcg<T>(P.uLx + i), x1 = ldcg<T>(P.uLx + iu);
+        const Acc y0 = ldcg<T>(P.uLy + i), y1 = ldcg<T>(P.uLy + il);
+        Acc wx0 = 1, wx1 = 1, wy0 = 1, wy1 = 1;
+        if (wtd) { wx0 = to_acc(P.a0x[i]); wx1 = to_acc(P.a0x[iu]); wy0 = to_acc(P.a0y[i]); wy1 = to_acc(P.a0y[il]); }
+        if (!init) v = ldcg<T>(P.v + i);
+        if (dn) l -= x0 * wx0;
+        if (up) l += x1 * wx1;
+        if (rt) l -= y0 * wy0;
+        if (lf) l += y1 * wy1;
+      }
+      lt[j] = l;
+      vo[j] = v;
+    }
+  }
+  gather_tile<true, T, Acc>(P.uA, m, r0, c0, g, Acc(1), sx);
+  load_bands<Acc>(P.op, true, 0, r0, c0, g, sbr, sbc);
+  if (h.done) return false;
   Acc At[PIX] = {};
-  __syncthreads();
-  load_tile_cg<T, Acc>(P.uA, m, r0, c0, g, inv_beta, sx);
-  tile_conv<Acc>(P.op, true, r0, c0, g, sx, sz, sbr, sbc, At);
-  const Acc sg = (Acc)sqrt(P.gamma);
-  const Acc ba = (!init && S.alpha > 0.0) ? (Acc)(S.beta / S.alpha) : Acc(0);
+  tile_conv<Acc>(P.op, true, r0, c0, g, sx, sz, sbr, sbc, At, true);
+  const Acc ib = h.K.inv_beta;                    // u = u~ / beta
+  const Acc sgb = P.sg * ib;
+  const Acc ba = init ? Acc(0) : h.K.ba;
   const int r = r0 + threadIdx.x;
   Acc s_v = 0;
-  const bool wtd = (P.solver == 0);
 #pragma unroll
   for (int j = 0; j < PIX; ++j) {
     const int c = c0 + threadIdx.y + TY * j;
     if (r >= m || c >= m) continue;
     const size_t i = r + (size_t)c * m;
-    Acc lt = 0;
-    if (r < m - 1) lt -= ldcg<T>(P.uLx + i) * (wtd ? to_acc(P.a0x[i]) : Acc(1));
-    if (r > 0) lt += ldcg<T>(P.uLx + i - 1) * (wtd ? to_acc(P.a0x[i - 1]) : Acc(1));
-    if (c < m - 1) lt -= ldcg<T>(P.uLy + i) * (wtd ? to_acc(P.a0y[i]) : Acc(1));
-    if (c > 0) lt += ldcg<T>(P.uLy + i - m) * (wtd ? to_acc(P.a0y[i - m]) : Acc(1));
-    Acc vt = At[j] + sg * inv_beta * lt;
-    if (!init) vt -= ba * ldcg<T>(P.v + i);
+    Acc vt = ib * At[j] + sgb * lt[j];
+    if (!init) vt -= ba * vo[j];
     P.v[i] = store_cast<T, Acc>(vt);
     s_v += vt * vt;
   }
-  red[0] = (double)s_v;
-  red[1] = 0.0;
-  red[2] = 0.0;
+  red[0] = s_v;
+  red[1] = Acc(0);
+  red[2] = Acc(0);
+  return true;
 }
 
-// Scalar work of the block that finished a problem's last tile.
-__device__ __forceinline__ void lsqr_finish_F(const LsqrCtl& ctl, LsqrState* st, bool init, int it,
-                                              const double (&tot)[3]) {
-  LsqrState S = load_state(st);
-  const double beta_new = sqrt(tot[0]);
+// Scalar work once every tile of a problem has reported (run by one thread).
+// Norms come from one rsqrt each (value = x * rsqrt(x)); the stopping tests
+// compare squares, so no square root or divide is needed for them:
+//   S1  rnorm <= btol*bnorm + atol*anorm*xnorm
+//   S2  arnorm <= atol*anorm*rnorm          (anorm, rnorm > 0)
+//   S3  anorm*||D_k||_F >= conlim
+template <typename Acc>
+__device__ __forceinline__ int lsqr_finish_F(const LsqrCtl& ctl, LsqrState S, LsqrState* st, LsqrCoef<Acc>* K,
+                                             bool init, int it, const double (&tot)[3]) {
+  const double ib = tot[0] > 0.0 ? rsqrt(tot[0]) : 0.0;
+  const double beta_new = tot[0] * ib;
   if (init) {
     S.beta = beta_new;
     S.bnorm = beta_new;
@@ -242,15 +288,14 @@ __device__ __forceinline__ void lsqr_finish_F(const LsqrCtl& ctl, LsqrState* st,
   } else {
     if (it >= 2) {
       const int k = it - 1;           // iteration being tested
-      S.dnorm2 += tot[2] / (S.rho_last * S.rho_last);
-      const double xnorm = sqrt(tot[1]);
-      const double anorm = sqrt(S.anorm2);
-      const double acond = anorm * sqrt(S.dnorm2);
+      S.dnorm2 += tot[2] * (S.irho_last * S.irho_last);
+      const double xnorm2 = tot[1];
       const double rnorm = S.t_rnorm, arnorm = S.t_arnorm;
+      const double lhs = rnorm - ctl.btol * S.bnorm;
       int stop = 0;
-      if (rnorm <= ctl.btol * S.bnorm + ctl.atol * anorm * xnorm) stop = 1;
-      else if (anorm > 0.0 && rnorm > 0.0 && arnorm <= ctl.atol * anorm * rnorm) stop = 2;
-      else if (acond >= ctl.conlim) stop = 3;
+      if (lhs <= 0.0 || lhs * lhs <= ctl.atol * ctl.atol * S.anorm2 * xnorm2) stop = 1;
+      else if (S.anorm2 > 0.0 && rnorm > 0.0 && arnorm * arnorm <= ctl.atol * ctl.atol * S.anorm2 * rnorm * rnorm) stop = 2;
+      else if (S.anorm2 * S.dnorm2 >= ctl.conlim * ctl.conlim) stop = 3;
       else if (k >= ctl.maxit) stop = 4;
       if (stop) { S.done = 1; S.stop = stop; S.its = k; }
     }
@@ -258,11 +303,17 @@ __device__ __forceinline__ void lsqr_finish_F(const LsqrCtl& ctl, LsqrState* st,
     S.it = it;
   }
   *st = S;
+  // coefficients of pass B: u = u~ / beta_{i+1}, v~ -= (beta_{i+1} / alpha_i) v~
+  K->inv_beta = (Acc)ib;
+  K->ba = (!init && S.alpha > 0.0) ? (Acc)(beta_new * (double)K->inv_alpha) : Acc(0);
+  return S.done;
 }
 
-__device__ __forceinline__ void lsqr_finish_B(LsqrState* st, bool init, const double (&tot)[3]) {
-  LsqrState S = load_state(st);
-  const double alpha_new = sqrt(tot[0]);
+template <typename Acc>
+__device__ __forceinline__ int lsqr_finish_B(LsqrState S, LsqrState* st, LsqrCoef<Acc>* K, bool init,
+                                             const double (&tot)[3]) {
+  const double ia = tot[0] > 0.0 ? rsqrt(tot[0]) : 0.0;
+  const double alpha_new = tot[0] * ia;
   if (init) {
     S.alpha = alpha_new;
     S.rhobar = alpha_new;
@@ -274,70 +325,146 @@ __device__ __forceinline__ void lsqr_finish_B(LsqrState* st, bool init, const do
   } else {
     const double alpha = S.alpha, beta = S.beta;
     S.anorm2 += alpha * alpha + beta * beta;
-    const double rho = sqrt(S.rhobar * S.rhobar + beta * beta);
-    const double c = S.rhobar / rho, s = beta / rho;
+    const double rho2 = S.rhobar * S.rhobar + beta * beta;
+    const double irho = rsqrt(rho2);        // one rsqrt gives 1/rho
+    const double c = S.rhobar * irho, s = beta * irho;
     const double theta = s * alpha_new;
     S.rhobar = -c * alpha_new;
     const double phi = c * S.phibar;
     S.phibar = s * S.phibar;
-    S.phi_rho = phi / rho;
-    S.theta_rho = theta / rho;
-    S.rho_last = rho;
+    S.phi_rho = phi * irho;
+    S.theta_rho = theta * irho;
+    S.irho_last = irho;
     S.t_rnorm = S.phibar;
     S.t_arnorm = S.phibar * alpha_new * fabs(c);
     S.alpha = alpha_new;
   }
   *st = S;
+  // coefficients of the next pass F
+  K->inv_alpha = (Acc)ia;
+  K->ab = S.beta > 0.0 ? (Acc)(S.alpha * (double)K->inv_beta) : Acc(0);
+  K->phr = (Acc)S.phi_rho;
+  K->thr = (Acc)S.theta_rho;
+  return S.done;
 }
 
-__device__ __forceinline__ bool all_done(const LsqrCtl& ctl) {
-  for (int p = 0; p < ctl.nprob; ++p)
-    if (__ldcg(&ctl.st[p].done) == 0) return false;
-  return true;
+// End of a phase: every block has written its tiles' partials. The last block
+// to arrive at the grid barrier reduces every problem's partials (warp w takes
+// problems w, w + 8, ...; fixed order over tiles), runs the scalar updates,
+// decides whether all problems have stopped, and only then releases the
+// others. Returns 0 to continue, 1 when all problems are done, -1 on timeout.
+template <typename T, typename Acc>
+__device__ int lsqr_phase_end(const LsqrProb<T, Acc>* probs, const LsqrCtl& ctl, LsqrCoef<Acc>* coef, bool isF,
+                              int it) {
+  __shared__ int s_last, s_ok, s_dec, s_live;
+  __shared__ unsigned s_gen;
+  GridBarrier* gb = ctl.gb;
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  using aref = cuda::atomic_ref<unsigned, cuda::thread_scope_device>;
+  __syncthreads();
+  if (tid == 0) {
+    s_ok = (*(volatile int*)&gb->error == 0);
+    s_last = 0;
+    s_live = 0;
+    if (s_ok) {
+      s_gen = aref(gb->gen).load(cuda::memory_order_relaxed);
+      // release: this block's writes of the phase (ordered before by the
+      // block barrier) become visible to whoever acquires the counter
+      s_last = (aref(gb->count).fetch_add(1u, cuda::memory_order_acq_rel) == gridDim.x - 1);
+    }
+  }
+  __syncthreads();
+  if (!s_ok) return -1;
+  if (s_last) {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int p = warp; p < ctl.nprob; p += (32 * TY) / 32) {
+      const LsqrProb<T, Acc>& P = probs[p];
+      // state and tile partials requested together; partials in batches of
+      // PB per lane (one memory round trip per batch), summed in tile order
+      constexpr int PB = 8;
+      LsqrState S;
+      if (lane == 0) S = load_state(&ctl.st[p]);
+      const double* part = ctl.part + (size_t)P.tile_begin * 3;
+      double tot[3] = {0.0, 0.0, 0.0};
+      for (int t0 = lane; t0 < P.ntiles; t0 += 32 * PB) {
+        double q[PB][3];
+#pragma unroll
+        for (int b = 0; b < PB; ++b) {
+          const int t = t0 + 32 * b;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) q[b][k] = t < P.ntiles ? __ldcg(part + (size_t)t * 3 + k) : 0.0;
+        }
+#pragma unroll
+        for (int b = 0; b < PB; ++b)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) tot[k] += q[b][k];
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) tot[k] = warp_sum(tot[k]);
+      if (lane == 0 && !S.done) {
+        const int done = isF ? lsqr_finish_F<Acc>(ctl, S, &ctl.st[p], coef + p, it == 0, it, tot)
+                             : lsqr_finish_B<Acc>(S, &ctl.st[p], coef + p, it == 0, tot);
+        if (!done) s_live = 1;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const int all = s_live ? 0 : 1;
+      gb->decision = all;
+      gb->count = 0;
+      // release: the scalar updates of this block become visible with the new generation
+      aref(gb->gen).fetch_add(1u, cuda::memory_order_release);
+      s_dec = all;
+    }
+  } else if (tid == 0) {
+    const unsigned long long t0 = globaltimer_ns();
+    unsigned spins = 0;
+    int ok = 1;
+    while (aref(gb->gen).load(cuda::memory_order_acquire) == s_gen) {
+      if (*(volatile int*)&gb->error) { ok = 0; break; }
+      if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > ctl.limit_ns) {
+        atomicExch(&gb->error, 1);
+        ok = 0;
+        break;
+      }
+    }
+    s_dec = ok ? *(volatile int*)&gb->decision : -1;
+  }
+  __syncthreads();
+  return s_dec;
 }
 
 template <typename T, typename Acc>
-__global__ void __launch_bounds__(256) k_lsqr(const LsqrProb<T, Acc>* __restrict__ probs, LsqrCtl ctl) {
+__global__ void __launch_bounds__(256, 2) k_lsqr(const LsqrProb<T, Acc>* __restrict__ probs, LsqrCtl ctl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Acc* sm = reinterpret_cast<Acc*>(smem_raw);
   __shared__ double scratch[3 * 32];
-  __shared__ int s_flag;
-  __shared__ LsqrState s_st;
+  LsqrCoef<Acc>* coef = reinterpret_cast<LsqrCoef<Acc>*>(ctl.coef);
   const unsigned G = gridDim.x;
   // phase 0: F(init), B(init); then F_i, B_i for i = 1, 2, ... until every
-  // problem has stopped (decided at each barrier by the last block to arrive)
-  auto decide = [&]() -> int { return all_done(ctl) ? 1 : 0; };
+  // problem has stopped (decided by the last block at each barrier)
   for (int it = 0;; ++it) {
     for (int half = 0; half < 2; ++half) {
       const bool isF = (half == 0);
       for (int tile = blockIdx.x; tile < ctl.ntiles; tile += G) {
-        const int p = ctl.tile_prob[tile];
+        const int p = __ldg(ctl.tile_prob + tile);
         const LsqrProb<T, Acc>& P = probs[p];
-        __syncthreads();
-        if (threadIdx.x == 0 && threadIdx.y == 0) s_st = load_state(&ctl.st[p]);
-        __syncthreads();
-        if (s_st.done) continue;
         const int tl = tile - P.tile_begin;
         const int r0 = (tl % P.nt) * TM, c0 = (tl / P.nt) * TN;
-        double red[3];
-        if (isF) lsqr_pass_F<T, Acc>(P, s_st, it == 0, it == 1, r0, c0, sm, red);
-        else lsqr_pass_B<T, Acc>(P, s_st, it == 0, r0, c0, sm, red);
-        if (finish_tile<3>(red, ctl.part, ctl.cnt, tile, p, P.ntiles, scratch, &s_flag)) {
-          if (threadIdx.y == 0) {
-            double tot[3];
-            problem_sum<3>(ctl.part, P.tile_begin, P.ntiles, tot);
-            if (threadIdx.x == 0) {
-              if (isF) lsqr_finish_F(ctl, &ctl.st[p], it == 0, it, tot);
-              else lsqr_finish_B(&ctl.st[p], it == 0, tot);
-              ctl.cnt[p] = 0;
-              __threadfence();
-            }
-          }
+        Acc red[3];
+        __syncthreads();   // shared memory of the previous tile is free
+        const bool did = isF ? lsqr_pass_F<T, Acc>(P, ctl, p, it == 0, it == 1, r0, c0, sm, red)
+                             : lsqr_pass_B<T, Acc>(P, ctl, p, it == 0, r0, c0, sm, red);
+        if (!did) continue;   // uniform over the block
+        double tot[3];
+        block_sum_to0<3, Acc>(red, tot, scratch);
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) ctl.part[(size_t)tile * 3 + k] = tot[k];
         }
       }
-      int stop = 0;
-      if (!grid_sync(ctl.gb, G, ctl.limit_ns, decide, &stop)) return;
-      if (stop) return;
+      const int dec = lsqr_phase_end<T, Acc>(probs, ctl, coef, isF, it);
+      if (dec != 0) return;
     }
   }
 }

@@ -59,68 +59,182 @@ __host__ __device__ inline int tile_smem_elems(int H, int w) {
   return H * H + H * TM + 2 * TM * band_pitch(w);
 }
 
-// Load X over the tile [r0+lo, r0+TM-1+hi] x [c0+lo, c0+TN-1+hi] (indices
-// wrapped mod m) scaled by `scale`, into sx[col][row] (pitch H).
-template <typename T, typename Acc>
-__device__ __forceinline__ void load_tile(const T* __restrict__ X, int m, int r0, int c0,
-                                          const TileGeom& g, Acc scale, Acc* sx) {
-  const int tid = threadIdx.x + 32 * threadIdx.y;
-  const int H = g.H;
-  for (int idx = tid; idx < H * H; idx += 32 * TY) {
-    int cc = idx / H, rr = idx - cc * H;
-    int gr = wrap(r0 + g.lo + rr, m), gc = wrap(c0 + g.lo + cc, m);
-    sx[idx] = to_acc(X[gr + (size_t)gc * m]) * scale;
+// Global -> register load; CG bypasses L1 (data written earlier in the same
+// launch by other blocks).
+template <bool CG, typename T>
+__device__ __forceinline__ typename Traits<T>::Acc gload(const T* p) {
+  if constexpr (CG) {
+    if constexpr (sizeof(T) == 2) {
+      unsigned short u = __ldcg(reinterpret_cast<const unsigned short*>(p));
+      return to_acc(*reinterpret_cast<const T*>(&u));
+    } else {
+      return __ldcg(p);
+    }
+  } else {
+    return to_acc(*p);
   }
 }
 
-// out[j] += (A or A^T applied to the tile in sx) at pixel (r0+tx, c0+ty+8j).
-// Caller has loaded sx (and synchronised). Uses sz/sb scratch.
-template <typename Acc>
-__device__ __forceinline__ void tile_conv(const BandOp<Acc>& op, bool tr, int r0, int c0,
-                                          const TileGeom& g, const Acc* sx, Acc* sz, Acc* sbr,
-                                          Acc* sbc, Acc (&out)[PIX]) {
-  const int m = op.m, w = g.w, pw = band_pitch(w), H = g.H;
+constexpr int GATHER_BATCH = 12;   // loads a thread keeps in flight per gather batch
+
+// Load X over the tile [r0+lo, r0+TM-1+hi] x [c0+lo, c0+TN-1+hi] (indices
+// wrapped mod m) scaled by `scale`, into sx[col][row] (pitch H). Each thread
+// issues a batch of GATHER_BATCH loads before its first shared-memory store,
+// so the window costs one memory round trip per batch (one batch for bands
+// up to 23 wide) rather than one per element.
+template <bool CG, typename T, typename Acc>
+__device__ __forceinline__ void gather_tile(const T* __restrict__ X, int m, int r0, int c0,
+                                            const TileGeom& g, Acc scale, Acc* sx) {
+  constexpr int NT = 32 * TY;
   const int tid = threadIdx.x + 32 * threadIdx.y;
-  const Acc* BR = tr ? op.brT : op.br;
-  const Acc* BC = tr ? op.bcT : op.bc;
-  const int r = threadIdx.x;
-  for (int t = 0; t < op.nterms; ++t) {
-    __syncthreads();
-    for (int idx = tid; idx < TM * w; idx += 32 * TY) {
-      int rr = idx / w, k = idx - rr * w;
-      sbr[rr * pw + k] = BR[((size_t)t * m + wrap(r0 + rr, m)) * w + k];
-      sbc[rr * pw + k] = BC[((size_t)t * m + wrap(c0 + rr, m)) * w + k];
+  const int H = g.H, HH = H * H;
+  const int dc = NT / H, dr = NT - dc * H;      // idx += NT  ->  (col, row) += (dc, dr), with carry
+  int cc = tid / H, rr = tid - cc * H;
+  const int rb = r0 + g.lo, cb = c0 + g.lo;
+  for (int base = tid; base < HH; base += NT * GATHER_BATCH) {
+    Acc v[GATHER_BATCH];
+#pragma unroll
+    for (int q = 0; q < GATHER_BATCH; ++q) {
+      v[q] = Acc(0);
+      if (base + q * NT < HH) v[q] = gload<CG, T>(X + wrap(rb + rr, m) + (size_t)wrap(cb + cc, m) * m);
+      rr += dr;
+      cc += dc;
+      if (rr >= H) { rr -= H; ++cc; }
     }
-    __syncthreads();
-    // step 1: along r with the row factor, for every loaded column
-    {
-      const Acc* brow = sbr + r * pw;
-      const int off = r - g.lo + g.dlo;
+#pragma unroll
+    for (int q = 0; q < GATHER_BATCH; ++q)
+      if (base + q * NT < HH) sx[base + q * NT] = v[q] * scale;
+  }
+}
+
+template <typename T, typename Acc>
+__device__ __forceinline__ void load_tile(const T* __restrict__ X, int m, int r0, int c0,
+                                          const TileGeom& g, Acc scale, Acc* sx) {
+  gather_tile<false, T, Acc>(X, m, r0, c0, g, scale, sx);
+}
+
+// Bands of term t for the tile's rows / columns into shared memory (loads of
+// a batch issued before the stores, as in gather_tile).
+template <typename Acc>
+__device__ __forceinline__ void load_bands(const BandOp<Acc>& op, bool tr, int t, int r0, int c0, const TileGeom& g,
+                                           Acc* sbr, Acc* sbc) {
+  constexpr int NT = 32 * TY, NB = 4;
+  const int m = op.m, w = g.w, pw = band_pitch(w);
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  const Acc* BR = (tr ? op.brT : op.br) + (size_t)t * m * w;
+  const Acc* BC = (tr ? op.bcT : op.bc) + (size_t)t * m * w;
+  const int n = TM * w;
+  for (int base = tid; base < n; base += NT * NB) {
+    Acc a[NB], b[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int idx = base + q * NT;
+      a[q] = b[q] = Acc(0);
+      if (idx < n) {
+        const int rr = idx / w, k = idx - rr * w;
+        a[q] = BR[(size_t)wrap(r0 + rr, m) * w + k];
+        b[q] = BC[(size_t)wrap(c0 + rr, m) * w + k];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int idx = base + q * NT;
+      if (idx < n) {
+        const int rr = idx / w, k = idx - rr * w;
+        sbr[rr * pw + k] = a[q];
+        sbc[rr * pw + k] = b[q];
+      }
+    }
+  }
+}
+
+// The two 1-D passes of one separable term. KW > 0: bands at most KW wide,
+// loops fully unrolled (every shared-memory load of an output issued before
+// its FMAs, taps of step 1 held in registers, two partial sums); KW == 0:
+// any width, runtime loop.
+template <int KW, typename Acc>
+__device__ __forceinline__ void conv_term(const TileGeom& g, const Acc* sx, Acc* sz, const Acc* sbr,
+                                          const Acc* sbc, Acc (&out)[PIX]) {
+  const int w = g.w, pw = band_pitch(w), H = g.H;
+  const int r = threadIdx.x;
+  // step 1: along r with the row factor, for every loaded column
+  {
+    const Acc* brow = sbr + r * pw;
+    const int off = r - g.lo + g.dlo;
+    if constexpr (KW > 0) {
+      Acc bk[KW];
+#pragma unroll
+      for (int k = 0; k < KW; ++k) bk[k] = (k < w) ? brow[k] : Acc(0);
+      for (int cz = threadIdx.y; cz < H; cz += TY) {
+        const Acc* xs = sx + cz * H + off;
+        Acc a0 = 0, a1 = 0;
+#pragma unroll
+        for (int k = 0; k < KW; k += 2) {
+          if (k < w) a0 += bk[k] * xs[k];
+          if (k + 1 < w) a1 += bk[k + 1] * xs[k + 1];
+        }
+        sz[cz * TM + r] = a0 + a1;
+      }
+    } else {
       for (int cz = threadIdx.y; cz < H; cz += TY) {
         const Acc* xs = sx + cz * H + off;
         Acc acc = 0;
+#pragma unroll 4
         for (int k = 0; k < w; ++k) acc += brow[k] * xs[k];
         sz[cz * TM + r] = acc;
       }
     }
-    __syncthreads();
-    // step 2: along c with the column factor
+  }
+  __syncthreads();
+  // step 2: along c with the column factor
 #pragma unroll
-    for (int j = 0; j < PIX; ++j) {
-      const int c = threadIdx.y + TY * j;
-      const Acc* bcol = sbc + c * pw;
-      const Acc* zs = sz + (c - g.lo + g.dlo) * TM + r;
+  for (int j = 0; j < PIX; ++j) {
+    const int c = threadIdx.y + TY * j;
+    const Acc* bcol = sbc + c * pw;
+    const Acc* zs = sz + (c - g.lo + g.dlo) * TM + r;
+    if constexpr (KW > 0) {
+      Acc a0 = 0, a1 = 0;
+#pragma unroll
+      for (int k = 0; k < KW; k += 2) {
+        if (k < w) a0 += bcol[k] * zs[k * TM];
+        if (k + 1 < w) a1 += bcol[k + 1] * zs[(k + 1) * TM];
+      }
+      out[j] += a0 + a1;
+    } else {
       Acc acc = 0;
+#pragma unroll 4
       for (int k = 0; k < w; ++k) acc += bcol[k] * zs[k * TM];
       out[j] += acc;
     }
   }
 }
 
+// out[j] += (A or A^T applied to the tile in sx) at pixel (r0+tx, c0+ty+8j).
+// Caller has loaded sx (and synchronised). Uses sz/sb scratch.
+// `first_loaded`: the caller already loaded term 0's bands (together with the
+// tile, before one barrier).
+template <typename Acc>
+__device__ __forceinline__ void tile_conv(const BandOp<Acc>& op, bool tr, int r0, int c0,
+                                          const TileGeom& g, const Acc* sx, Acc* sz, Acc* sbr,
+                                          Acc* sbc, Acc (&out)[PIX], bool first_loaded = false) {
+  for (int t = 0; t < op.nterms; ++t) {
+    if (!(t == 0 && first_loaded)) {
+      __syncthreads();
+      load_bands<Acc>(op, tr, t, r0, c0, g, sbr, sbc);
+    }
+    __syncthreads();
+    if (g.w <= 16) conv_term<16, Acc>(g, sx, sz, sbr, sbc, out);
+    else conv_term<0, Acc>(g, sx, sz, sbr, sbc, out);
+  }
+}
+
 // ---- standalone blur apply: Y = scale * A X (or A^T X) ----------------------
+// `nrm2` (optional, device): the input is scaled by 1/sqrt(*nrm2) on load;
+// `xcopy` (optional): the scaled input is also written there (own pixels).
 template <typename T, typename Acc>
 __global__ void __launch_bounds__(256) k_blur(BandOp<Acc> op, int tr, const T* __restrict__ X,
-                                              T* __restrict__ Y, Acc scale) {
+                                              T* __restrict__ Y, Acc scale, const double* nrm2 = nullptr,
+                                              T* xcopy = nullptr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Acc* sm = reinterpret_cast<Acc*>(smem_raw);
   const int m = op.m;
@@ -130,6 +244,7 @@ __global__ void __launch_bounds__(256) k_blur(BandOp<Acc> op, int tr, const T* _
   Acc* sbr = sz + g.H * TM;
   Acc* sbc = sbr + TM * band_pitch(g.w);
   const int nt = (m + TM - 1) / TM;
+  if (nrm2) scale = (Acc)(1.0 / sqrt(*nrm2));
   for (int tile = blockIdx.x; tile < nt * nt; tile += gridDim.x) {
     const int r0 = (tile % nt) * TM, c0 = (tile / nt) * TN;
     __syncthreads();
@@ -140,7 +255,10 @@ __global__ void __launch_bounds__(256) k_blur(BandOp<Acc> op, int tr, const T* _
 #pragma unroll
     for (int j = 0; j < PIX; ++j) {
       const int c = c0 + threadIdx.y + TY * j;
-      if (r < m && c < m) Y[r + (size_t)c * m] = store_cast<T, Acc>(out[j]);
+      if (r < m && c < m) {
+        Y[r + (size_t)c * m] = store_cast<T, Acc>(out[j]);
+        if (xcopy) xcopy[r + (size_t)c * m] = store_cast<T, Acc>(sx[(threadIdx.y + TY * j - g.lo) * g.H + threadIdx.x - g.lo]);
+      }
     }
   }
 }
@@ -307,68 +425,69 @@ __global__ void k_fine_bands_d(int m, int S, int nterms, const double* __restric
 // ---- PSF factorisation: one-sided Jacobi SVD (Hestenes) in double -------------
 // P (S x S, column-major P[p + q*S], p = row offset index) = sum_t s_t u_t v_t^T.
 // Output: nterms, row factors fr[t][p] = s_t u_t(p), column factors fc[t][q] = v_t(q),
-// for singular values above rel_tol * s_1. One block; S <= 64.
-__global__ void k_psf_svd(int S, const double* __restrict__ P, double rel_tol, int* nterms,
-                          double* fr, double* fc, double* work) {
+// for singular values above rel_tol * s_1. One block of 256 threads; S <= 64.
+// Columns are rotated in tournament order: each round pairs every column with
+// another (S/2 disjoint pairs, one warp per pair, lanes over the S rows), so a
+// sweep is S-1 parallel rounds instead of S(S-1)/2 serial rotations.
+__global__ void __launch_bounds__(256) k_psf_svd(int S, const double* __restrict__ P, double rel_tol, int* nterms,
+                                                 double* fr, double* fc, double* work) {
   // work: U (S*S) columns = P's columns rotated, V (S*S), norms (S)
   double* U = work;
   double* V = work + S * S;
   double* nrm = work + 2 * S * S;
-  __shared__ double s_c, s_s;
   __shared__ int s_rot;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   for (int i = tid; i < S * S; i += blockDim.x) {
     U[i] = P[i];                       // columns of P, indexed U[p + q*S]
     V[i] = ((i % S) == (i / S)) ? 1.0 : 0.0;
   }
-  __syncthreads();
+  const int np = S + (S & 1);          // players (one dummy when S is odd)
   for (int sweep = 0; sweep < 60; ++sweep) {
     if (tid == 0) s_rot = 0;
     __syncthreads();
-    for (int i = 0; i < S - 1; ++i) {
-      for (int j = i + 1; j < S; ++j) {
-        if (tid == 0) {
-          double a = 0, b = 0, g = 0;
-          for (int p = 0; p < S; ++p) {
-            double ui = U[p + i * S], uj = U[p + j * S];
-            a += ui * ui; b += uj * uj; g += ui * uj;
-          }
-          double c = 1.0, s = 0.0;
-          if (fabs(g) > 1e-300 && fabs(g) > 1e-15 * sqrt(a * b)) {
-            double zeta = (b - a) / (2.0 * g);
-            double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = c * t;
-            s_rot = 1;
-          }
-          s_c = c; s_s = s;
+    for (int round = 0; round < np - 1; ++round) {
+      for (int k = warp; k < np / 2; k += nwarp) {
+        // round-robin schedule: player 0 fixed, the others rotate
+        const int a0 = k, b0 = np - 1 - k;
+        int i = a0 == 0 ? 0 : 1 + (a0 - 1 + round) % (np - 1);
+        int j = 1 + (b0 - 1 + round) % (np - 1);
+        if (i >= S || j >= S) continue;          // dummy player
+        if (i > j) { const int t = i; i = j; j = t; }
+        double a = 0, b = 0, g = 0;
+        for (int p = lane; p < S; p += 32) {
+          const double ui = U[p + i * S], uj = U[p + j * S];
+          a += ui * ui; b += uj * uj; g += ui * uj;
         }
-        __syncthreads();
-        const double c = s_c, s = s_s;
-        if (s != 0.0) {
-          for (int p = tid; p < S; p += blockDim.x) {
-            double ui = U[p + i * S], uj = U[p + j * S];
-            U[p + i * S] = c * ui - s * uj;
-            U[p + j * S] = s * ui + c * uj;
-            double vi = V[p + i * S], vj = V[p + j * S];
-            V[p + i * S] = c * vi - s * vj;
-            V[p + j * S] = s * vi + c * vj;
+        a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
+        if (fabs(g) > 1e-300 && fabs(g) > 1e-15 * sqrt(a * b)) {
+          const double zeta = (b - a) / (2.0 * g);
+          const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+          for (int p = lane; p < S; p += 32) {
+            const double ui = U[p + i * S], uj = U[p + j * S];
+            U[p + i * S] = c * ui - sn * uj;
+            U[p + j * S] = sn * ui + c * uj;
+            const double vi = V[p + i * S], vj = V[p + j * S];
+            V[p + i * S] = c * vi - sn * vj;
+            V[p + j * S] = sn * vi + c * vj;
           }
+          if (lane == 0) s_rot = 1;
         }
-        __syncthreads();
       }
+      __syncthreads();
     }
-    __syncthreads();
     if (s_rot == 0) break;
     __syncthreads();
   }
   // P V = U (orthogonal columns): P = sum_j U_j V_j^T. Sort by norm.
+  for (int j = warp; j < S; j += nwarp) {
+    double a = 0;
+    for (int p = lane; p < S; p += 32) a += U[p + j * S] * U[p + j * S];
+    a = warp_sum(a);
+    if (lane == 0) nrm[j] = sqrt(a);
+  }
+  __syncthreads();
   if (tid == 0) {
-    for (int j = 0; j < S; ++j) {
-      double a = 0;
-      for (int p = 0; p < S; ++p) a += U[p + j * S] * U[p + j * S];
-      nrm[j] = sqrt(a);
-    }
     double smax = 0;
     for (int j = 0; j < S; ++j) smax = fmax(smax, nrm[j]);
     int cnt = 0;

@@ -23,8 +23,9 @@ def problem(m, sigma=2.0, Sz=9, seed=0):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("kind", ["plain", "irls", "mm", "sb"])
-@pytest.mark.parametrize("m", [32, 64])
+@pytest.mark.parametrize("m", [16, 32, 64])
 def test_gcv_matches_oracle(prec, kind, m):
+    """m = 16 (256 pixels) runs the exact mode, m = 32, 64 the projected one."""
     import torch
     dt = torch.float64 if prec == "fp64" else torch.float32
     A, b, x_true, psf = problem(m)
@@ -51,3 +52,24 @@ def test_gcv_matches_oracle(prec, kind, m):
                        None if a0 is None else planes_to_dev(*a0, dt),
                        None if a1 is None else planes_to_dev(*a1, dt))
     assert abs(g - g_ref) <= max(1e-2, 10 * spread) * g_ref, (g, g_ref, g_sp)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind", ["plain", "mm"])
+def test_gcv_exact_mode_tiny_level(prec, kind):
+    """8 x 8 level with a 5 x 5 PSF: exact mode on both sides; the minimiser
+    lies at the small-gamma end, where only a cancellation-free numerator is
+    meaningful."""
+    import torch
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    A, b, x_true, psf = problem(8, 1.2, 5)
+    a0 = None
+    if kind == "mm":
+        qx, qy = O.L_apply(0.8 * x_true)
+        a0 = S.mm_surrogate(qx, qy, 0.03)
+    sub = S.Subproblem(A, b, c=a0)
+    g_ref = sub.gcv(S.opts_with())
+    g_sp = noisy(lambda: sub.gcv(S.opts_with()), prec)
+    g = api.gcv_select(psf, 8, "mm", img_to_dev(b, dt), None if a0 is None else planes_to_dev(*a0, dt))
+    tol = 1e-6 if prec == "fp64" else 1e-2
+    assert abs(g - g_ref) <= max(tol, 10 * abs(g_sp - g_ref) / g_ref) * g_ref, (g, g_ref, g_sp)

@@ -48,8 +48,11 @@ def test_lsqr_matches_oracle(prec, solver, m):
     sub = S.Subproblem(A, b, weights=a0 if solver == "irls" else None,
                        c=None if solver == "irls" else (a0 if solver == "mm" else (a0[0] - a1[0], a0[1] - a1[1])))
     x_ref, its_ref = sub.solve(gamma, x0, o)
-    x_sp, its_sp = noisy(lambda: sub.solve(gamma, x0, o), prec)
-    spread, spread_it = rel(x_sp, x_ref), abs(its_sp - its_ref)
+    # rounding spread of the oracle: largest distance over two perturbed reruns
+    reruns = [noisy(lambda: sub.solve(gamma, x0, o), prec, seed) for seed in (12345, 777)]
+    spread = max(rel(xs, x_ref) for xs, _ in reruns)
+    spread_it = max(abs(it - its_ref) for _, it in reruns)
+    its_sp = [it for _, it in reruns]
     xo = torch.empty(m * m, device="cuda", dtype=dt)
     its = api.lsqr_solve(psf, m, solver, gamma, img_to_dev(b, dt), img_to_dev(x0, dt),
                          planes_to_dev(*a0, dt), None if a1 is None else planes_to_dev(*a1, dt), xo)

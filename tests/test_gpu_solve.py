@@ -5,9 +5,11 @@ The method is sensitive to rounding-level perturbations (LSQR without
 reorthogonalisation stopped at its iteration limit, GCV on small coarse
 levels), so the oracle rerun with unit-roundoff noise of the storage
 precision injected into every operator output (tests/perturb.py) already
-differs from the plain oracle run. Each tolerance is the larger of the
-stated target (x: 1e-4 FP32, 1e-6 FP64; gamma: 1 %; outer iterations: +-1)
-and ten times that measured spread.
+differs from the plain oracle run. The spread is the largest distance from
+the plain run over two such reruns with independent noise (one rerun alone
+under-estimates it on the chaotic IRLS cycles). Each tolerance is the larger
+of the stated target (x: 1e-4 FP32, 1e-6 FP64; gamma: 1 %; outer
+iterations: +-1) and ten times that measured spread.
 """
 import numpy as np
 import pytest
@@ -41,21 +43,24 @@ def references(A, b, combo, prec):
     key = ("ref", id(A), combo, prec)
     if key not in _CACHE:
         r0 = S.mgm(b, A, *combo)
-        r1 = noisy(lambda: S.mgm(b, A, *combo), prec)
+        r1 = [noisy(lambda: S.mgm(b, A, *combo), prec, seed) for seed in (12345, 777)]
         _CACHE[key] = (r0, r1)
     return _CACHE[key]
 
 
 def compare(r, r0, r1, prec):
-    spread_x = rel(r1["x"], r0["x"])
+    """r1: the perturbed oracle reruns (a list, or one result)."""
+    runs = r1 if isinstance(r1, list) else [r1]
+    spread_x = max(rel(q["x"], r0["x"]) for q in runs)
     d = rel(r["x"], r0["x"])
     assert d <= max(XTOL[prec], 10 * spread_x), f"x rel diff {d:.2e} (oracle spread {spread_x:.2e})"
     for i in range(len(r0["iters"])):
-        spread_it = abs(r1["iters"][i] - r0["iters"][i])
-        assert abs(r["iters"][i] - r0["iters"][i]) <= max(1, 2 * spread_it), (i, r["iters"], r0["iters"], r1["iters"])
-        spread_mu = abs(r1["mu"][i] - r0["mu"][i]) / r0["mu"][i]
+        spread_it = max(abs(q["iters"][i] - r0["iters"][i]) for q in runs)
+        assert abs(r["iters"][i] - r0["iters"][i]) <= max(1, 2 * spread_it), \
+            (i, r["iters"], r0["iters"], [q["iters"] for q in runs])
+        spread_mu = max(abs(q["mu"][i] - r0["mu"][i]) for q in runs) / r0["mu"][i]
         dm = abs(r["mu"][i] - r0["mu"][i]) / r0["mu"][i]
-        assert dm <= max(1e-2, 10 * spread_mu), (i, r["mu"], r0["mu"], r1["mu"])
+        assert dm <= max(1e-2, 10 * spread_mu), (i, r["mu"], r0["mu"], [q["mu"] for q in runs])
     return d, spread_x
 
 
