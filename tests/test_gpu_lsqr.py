@@ -57,7 +57,7 @@ def test_lsqr_matches_oracle(prec, solver, m):
     its = api.lsqr_solve(psf, m, solver, gamma, img_to_dev(b, dt), img_to_dev(x0, dt),
                          planes_to_dev(*a0, dt), None if a1 is None else planes_to_dev(*a1, dt), xo)
     x = dev_to_img(xo, m)
-    target = 1e-10 if prec == "fp64" else 1e-5
+    target = 1e-10 if prec == "fp64" else 1e-4   # FP32 parity target: 1e-4 relative
     assert abs(its - its_ref) <= max(1, 2 * spread_it), (its, its_ref, its_sp)
     assert rel(x, x_ref) <= max(target, 10 * spread), (rel(x, x_ref), spread)
 
