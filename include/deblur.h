@@ -241,6 +241,25 @@ db_status db_lsqr_solve(db_context* ctx, const double* psf_host, int psf_size, i
                         void* x_out, const db_opts* opts, int* iters,
                         db_precision prec, db_stream stream);
 
+/* The same LSQR solve as db_lsqr_solve without a context and without any
+ * device allocation. The paper has no counterpart: this exists for callers
+ * that must not allocate device memory when they call (a process that gives
+ * all of HBM to its own pool, a loop that may not touch the allocator).
+ * All workspace comes from one 16 MiB array the library reserves when it is
+ * loaded; it limits m to 256 and psf_size to 31, and a problem whose
+ * workspace does not fit (e.g. a high-rank PSF) returns DB_EINVAL with a
+ * message in db_last_error(NULL); so do larger m or psf_size. Arguments,
+ * layouts and results are those of db_lsqr_solve; b, x0 and the auxiliary
+ * planes are read in place. The array is shared by every call on a device:
+ * calls that overlap in time race on it and must be serialised by the
+ * caller. The first call on a device looks the array up; make it before any
+ * stream capture begins. Synchronises `stream`. */
+db_status db_lsqr_solve_static(const double* psf_host, int psf_size, int m,
+                               db_solver solver, double gamma,
+                               const void* b, const void* x0, const void* aux0, const void* aux1,
+                               void* x_out, const db_opts* opts, int* iters,
+                               db_precision prec, db_stream stream);
+
 /* GCV choice of gamma (Sec. 3, projected form above) for the level-0
  * subproblem of the given solver with auxiliaries aux0/aux1 (device planes;
  * NULL = none: unweighted pair with zero shift). gamma_out on the host.

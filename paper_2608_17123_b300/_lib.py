@@ -86,6 +86,8 @@ _SIGS = {
     "db_aux_prolong": (C.c_int, [C.c_int, C.c_int, _VP, _VP, C.c_int, _VP]),
     "db_lsqr_solve": (C.c_int, [_VP, _VP, C.c_int, C.c_int, C.c_int, C.c_double, _VP, _VP, _VP, _VP, _VP,
                                 C.POINTER(DbOpts), C.POINTER(C.c_int), C.c_int, _VP]),
+    "db_lsqr_solve_static": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, C.c_double, _VP, _VP, _VP, _VP, _VP,
+                                       C.POINTER(DbOpts), C.POINTER(C.c_int), C.c_int, _VP]),
     "db_gcv_select": (C.c_int, [_VP, _VP, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, C.POINTER(DbGcvOpts),
                                 C.POINTER(C.c_double), C.c_int, _VP]),
 }

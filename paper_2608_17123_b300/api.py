@@ -199,6 +199,18 @@ def lsqr_solve(psf, m, solver, gamma, b, x0, aux0, aux1, x_out, ctx=None, stream
     return its.value
 
 
+def lsqr_solve_static(psf, m, solver, gamma, b, x0, aux0, aux1, x_out, stream=None, **options):
+    """db_lsqr_solve_static: lsqr_solve without a context or any device
+    allocation (static 16 MiB workspace; m <= 256, PSF <= 31 x 31)."""
+    pp = to_colmajor(np.asarray(psf, dtype=np.float64))
+    o, _ = make_opts("fp64" if _prec(b) == 0 else "fp32", **options)
+    its = C.c_int(0)
+    L.check(L.lib().db_lsqr_solve_static(pp.ctypes.data, pp.shape[0], m, L.SOLVERS[solver], gamma,
+                                         _ptr(b), _ptr(x0), _ptr(aux0), _ptr(aux1), _ptr(x_out), C.byref(o),
+                                         C.byref(its), _prec(b), _stream(stream)))
+    return its.value
+
+
 def gcv_select(psf, m, solver, b, aux0=None, aux1=None, ctx=None, stream=None, **options):
     ctx = ctx or default_context()
     pp = to_colmajor(np.asarray(psf, dtype=np.float64))

@@ -1923,3 +1923,203 @@ extern "C" db_status db_gcv_select(db_context* ctx, const double* psf_host, int 
   }
 }
 
+
+// ============================================================================
+// LSQR solve with a static workspace (no device allocation)
+// ============================================================================
+// db_lsqr_solve keeps its workspace in the context's arena, which grows with
+// cudaMalloc. Some callers must not allocate device memory when they call:
+// a process that hands all of HBM to its own memory pool at start-up (so a
+// later cudaMalloc fails or would steal from the pool), or a latency-bound
+// loop that may not take the allocator's synchronisation and fragmentation
+// risk per call. db_lsqr_solve_static serves them from one fixed array that
+// the module reserves when it is loaded, so the call allocates nothing.
+// The array is shared by every call on a device: calls that overlap in time
+// (two host threads, or two streams) race on it and must be serialised by
+// the caller. The first call on a device looks the array up once
+// (cudaGetSymbolAddress); make it before any stream capture begins.
+constexpr size_t NOALLOC_BYTES = (size_t)16 << 20;   // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Device address of the scratch array on the current device, looked up once
+// per device.
+static void* noalloc_base() {
+  static std::mutex mu;
+  static void* base[128] = {};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  REQUIRE(dev >= 0 && dev < 128, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(mu);
+  if (!base[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      throw DbError{DB_ECUDA, std::string("cudaGetSymbolAddress of the static workspace failed: ") +
+                                  cudaGetErrorString(e)};
+    }
+    base[dev] = p;
+  }
+  return base[dev];
+}
+
+// Bump allocator over the static array; running past its end is an input
+// error (the problem is too large for this entry point), not an allocation.
+struct StaticCursor {
+  char* base;
+  size_t off = 0;
+  template <typename X> X* take(size_t count) {
+    const size_t bytes = (count * sizeof(X) + 255) & ~size_t(255);
+    if (off + bytes > NOALLOC_BYTES)
+      throw DbError{DB_EINVAL, "problem too large for the 16 MiB static workspace of db_lsqr_solve_static"};
+    X* p = reinterpret_cast<X*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+template <typename T>
+static void static_lsqr(cudaStream_t st, const double* psf_host, int S, int m, db_solver solver, double gamma,
+                        const void* b, const void* x0, const void* aux0, const void* aux1, void* x_out,
+                        const db_opts& o, int* iters) {
+  using Acc = typename Traits<T>::Acc;
+  int dev = 0, nsm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  StaticCursor cur{static_cast<char*>(noalloc_base())};
+  const size_t n = (size_t)m * m;
+  // PSF factorisation (separable terms) into the workspace
+  double* dpsf = cur.take<double>((size_t)S * S);
+  double* wk = cur.take<double>((size_t)2 * S * S + S);
+  double* fr = cur.take<double>((size_t)S * S);
+  double* fc = cur.take<double>((size_t)S * S);
+  int* d_nt = cur.take<int>(1);
+  CK(cudaMemcpyAsync(dpsf, psf_host, (size_t)S * S * sizeof(double), cudaMemcpyHostToDevice, st));
+  k_psf_svd<<<1, 256, 0, st>>>(S, dpsf, 1e-13, d_nt, fr, fc, wk);
+  CK(cudaGetLastError());
+  int nterms = 0;
+  CK(cudaMemcpyAsync(&nterms, d_nt, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  REQUIRE(nterms >= 1, "PSF is zero");
+  // level-0 bands (zero-boundary blur, Sec. 5)
+  Level<T> L;
+  L.m = m;
+  L.n = n;
+  L.dlo = -(S / 2);
+  L.w = S;
+  const size_t nb = (size_t)nterms * m * S;
+  L.Bd_r = cur.take<double>(nb);
+  L.Bd_c = cur.take<double>(nb);
+  L.br = cur.take<Acc>(nb); L.bc = cur.take<Acc>(nb); L.brT = cur.take<Acc>(nb); L.bcT = cur.take<Acc>(nb);
+  const int gb = grid_for(nb, nsm);
+  k_fine_bands_d<<<gb, 256, 0, st>>>(m, S, nterms, fr, L.Bd_r);
+  k_fine_bands_d<<<gb, 256, 0, st>>>(m, S, nterms, fc, L.Bd_c);
+  k_transpose_band<Acc><<<gb, 256, 0, st>>>(m, L.dlo, L.w, nterms, L.Bd_r, L.br, L.brT);
+  k_transpose_band<Acc><<<gb, 256, 0, st>>>(m, L.dlo, L.w, nterms, L.Bd_c, L.bc, L.bcT);
+  CK(cudaGetLastError());
+  // LSQR vectors; the caller's b, x0 and auxiliary planes are read in place
+  L.uA = cur.take<T>(n); L.uLx = cur.take<T>(n); L.uLy = cur.take<T>(n);
+  L.v = cur.take<T>(n); L.wv = cur.take<T>(n); L.dlt = cur.take<T>(n);
+  const int gn = grid_for(n, nsm);
+  T* zeros = nullptr;     // x0 / shift planes the caller left out
+  T* ones = nullptr;      // unit IRLS weights
+  auto zero_plane = [&]() {
+    if (!zeros) { zeros = cur.take<T>(n); k_fill<T><<<gn, 256, 0, st>>>(n, zeros, 0.0); }
+    return zeros;
+  };
+  const T* a0 = static_cast<const T*>(aux0);
+  const T* a1 = static_cast<const T*>(aux1);
+  if (a0) { L.a0x = const_cast<T*>(a0); L.a0y = const_cast<T*>(a0) + n; }
+  else if (solver == DB_IRLS) {
+    ones = cur.take<T>(n);
+    k_fill<T><<<gn, 256, 0, st>>>(n, ones, 1.0);
+    L.a0x = L.a0y = ones;
+  } else { L.a0x = L.a0y = zero_plane(); }
+  if (a1) { L.a1x = const_cast<T*>(a1); L.a1y = const_cast<T*>(a1) + n; }
+  else { L.a1x = L.a1y = zero_plane(); }
+  const T* xstart = x0 ? static_cast<const T*>(x0) : zero_plane();
+  CK(cudaGetLastError());
+  // LSQR control block; the state, coefficients, tile counters and the grid
+  // barrier must start at zero
+  const int nt = L.ntiles_side();
+  const int ntiles = nt * nt;
+  double* d_part = cur.take<double>((size_t)std::max(ntiles * 3 + 64, 2 * 8 * nsm));
+  unsigned* d_cnt = cur.take<unsigned>(64);
+  double* d_box = cur.take<double>(64);
+  GridBarrier* d_gb = cur.take<GridBarrier>(1);
+  LsqrState* d_st = cur.take<LsqrState>(1);
+  LsqrCoef<Acc>* d_coef = cur.take<LsqrCoef<Acc>>(1);
+  LsqrProb<T, Acc>* d_prob = cur.take<LsqrProb<T, Acc>>(1);
+  int* d_tile_prob = cur.take<int>(ntiles);
+  CK(cudaMemsetAsync(d_cnt, 0, 64 * sizeof(unsigned), st));
+  CK(cudaMemsetAsync(d_gb, 0, sizeof(GridBarrier), st));
+  CK(cudaMemsetAsync(d_st, 0, sizeof(LsqrState), st));
+  CK(cudaMemsetAsync(d_coef, 0, sizeof(LsqrCoef<Acc>), st));
+  CK(cudaMemsetAsync(d_tile_prob, 0, sizeof(int) * ntiles, st));   // every tile belongs to problem 0
+  LsqrProb<T, Acc> P;
+  P.op = L.op(nterms);
+  P.m = m;
+  P.solver = solver;
+  P.gamma = gamma;
+  P.sg = (Acc)std::sqrt(gamma);
+  P.b = static_cast<const T*>(b);
+  P.x0 = o.lsqr_warm_start ? xstart : nullptr;
+  P.a0x = L.a0x; P.a0y = L.a0y; P.a1x = L.a1x; P.a1y = L.a1y;
+  P.uA = L.uA; P.uLx = L.uLx; P.uLy = L.uLy; P.v = L.v; P.w = L.wv; P.dlt = L.dlt;
+  P.nt = nt;
+  P.ntiles = ntiles;
+  P.tile_begin = 0;
+  CK(cudaMemcpyAsync(d_prob, &P, sizeof(P), cudaMemcpyHostToDevice, st));
+  LsqrCtl c;
+  c.atol = o.lsqr_atol; c.btol = o.lsqr_btol; c.conlim = o.lsqr_conlim; c.maxit = o.lsqr_maxit;
+  c.nprob = 1; c.ntiles = ntiles;
+  c.tile_prob = d_tile_prob; c.part = d_part; c.cnt = d_cnt; c.st = d_st; c.gb = d_gb; c.coef = d_coef;
+  c.limit_ns = 2000000000ull;
+  TileGeom g0 = tile_geom(P.op, false), g1 = tile_geom(P.op, true);
+  const int sm = std::max(tile_smem_elems(g0.H, g0.w), tile_smem_elems(g1.H, g1.w)) * (int)sizeof(Acc);
+  auto kfn = k_lsqr<T, Acc>;
+  if (sm > 48 * 1024) CK(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, sm));
+  REQUIRE(per_sm >= 1, "LSQR kernel does not fit on an SM");
+  const int grid = std::max(1, std::min(ntiles, per_sm * nsm));
+  const LsqrProb<T, Acc>* pp = d_prob;
+  void* args[] = {(void*)&pp, (void*)&c};
+  CK(cudaLaunchCooperativeKernel((const void*)kfn, dim3(grid), dim3(32, TY), args, sm, st));
+  // x_out = x0 + delta
+  k_outer_update<T><<<gn, 256, 0, st>>>(m, -1, o.lsqr_warm_start, xstart, L.dlt, static_cast<T*>(x_out), nullptr,
+                                        nullptr, nullptr, nullptr, 0, 0, 0, d_part, d_cnt + 4, d_box);
+  CK(cudaGetLastError());
+  LsqrState S_;
+  GridBarrier gbh;
+  CK(cudaMemcpyAsync(&S_, d_st, sizeof(S_), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&gbh, d_gb, sizeof(gbh), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (gbh.error) throw DbError{DB_ETIMEOUT, "LSQR grid barrier timed out"};
+  *iters = S_.its;
+}
+
+extern "C" db_status db_lsqr_solve_static(const double* psf_host, int S, int m, db_solver solver, double gamma,
+                                          const void* b, const void* x0, const void* aux0, const void* aux1,
+                                          void* x_out, const db_opts* opts, int* iters, db_precision prec,
+                                          db_stream stream) {
+  try {
+    REQUIRE(psf_host && b && x_out && iters, "null pointer argument");
+    validate(m, S, 1, DB_HAAR);
+    REQUIRE(m <= 256, "db_lsqr_solve_static takes images of at most 256 x 256 pixels");
+    REQUIRE(S <= 31, "db_lsqr_solve_static takes PSFs of at most 31 x 31");
+    REQUIRE(solver == DB_IRLS || solver == DB_MM || solver == DB_SB, "unknown solver");
+    REQUIRE(gamma > 0, "gamma must be positive");
+    db_opts o;
+    db_default_opts(&o, nullptr);
+    if (opts) o = *opts;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == DB_PREC_FP64) static_lsqr<double>(st, psf_host, S, m, solver, gamma, b, x0, aux0, aux1, x_out, o, iters);
+    else if (prec == DB_PREC_FP32) static_lsqr<float>(st, psf_host, S, m, solver, gamma, b, x0, aux0, aux1, x_out, o, iters);
+    else REQUIRE(false, "FP64 or FP32 only");
+    return DB_OK;
+  } catch (DbError& e) {
+    g_last_error = e.msg;
+    return e.st;
+  }
+}
