@@ -219,6 +219,12 @@ def run_ours(args, rank, world):
         e2e_ms += (time.perf_counter() - t0) * 1e3
     e2e_value = M * M * e2e_steps * world / (e2e_ms / 1e3) / 1e6
 
+    # batched and served forms on the same timed images (host buffers, like e2e)
+    forms = {}
+    if world == 1 and args.forms:
+        forms = run_forms(api, ctx, torch, [host_inputs[args.warmup + i] for i in range(args.steps)],
+                          [steps[args.warmup + i] for i in range(args.steps)], psf)
+
     # roofline of the dominant kernel (LSQR persistent kernel)
     peak, peak_kind = load_peaks()
     bytes_alg = (stats["lsqr_pixel_iters_irls"] * BYTES_PER_PIX_ITER["irls"]
@@ -245,7 +251,53 @@ def run_ours(args, rank, world):
         "counts": {"lsqr_launches": int(stats["lsqr_launches"]), "gcv_calls": int(stats["gcv_calls"]),
                    "outer_iterations": int(stats["outer_iterations"])},
     }
+    line.update(forms)
     return line, per_level_counts, times
+
+
+def run_forms(api, ctx, torch, bs, step_ids, psf):
+    """Images/s of the plain one-at-a-time host call, the batched call
+    (deblur_solve_batch) and the serving loop (db_server_*, all requests
+    queued at once) on the same images, with the largest relative difference
+    of the batched and served reconstructions from the plain ones."""
+    from paper_2608_17123_b300 import inputs as I
+    imgs = [I.from_colmajor(b, M) for b in bs]
+    specs = [step_spec(s) for s in step_ids]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [api.deblur_solve(b, psf, sp[0], sp[1], LEVELS, sp[2], precision="fp32", ctx=ctx)
+             for b, sp in zip(imgs, specs)]
+    t_plain = time.perf_counter() - t0
+    probs = [dict(b=b, psf=psf, solver=sp[0], wavelet=sp[1], levels=LEVELS, transfer=sp[2])
+             for b, sp in zip(imgs, specs)]
+    t0 = time.perf_counter()
+    batched = api.deblur_solve_batch(probs, precision="fp32", ctx=ctx)
+    t_batch = time.perf_counter() - t0
+    srv = api.Server(max_resident=len(imgs), max_m=M)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(b, psf, sp[0], sp[1], LEVELS, sp[2]) for b, sp in zip(imgs, specs)]
+    served, lat = [], []
+    for tk in tickets:
+        r, l = srv.poll(tk)
+        served.append(r)
+        lat.append(l)
+    t_srv = time.perf_counter() - t0
+    srv.close()
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    n = len(imgs)
+    lat_sorted = sorted(lat)
+    return {
+        "plain_images_per_s": round(n / t_plain, 4),
+        "batched": {"images_per_s": round(n / t_batch, 4), "images": n, "call": "deblur_solve_batch",
+                    "max_rel_diff_vs_plain": max(rel(b["x"], p["x"]) for b, p in zip(batched, plain))},
+        "serving": {"images_per_s": round(n / t_srv, 4), "requests": n, "arrival": "all queued at t=0",
+                    "p50_ms": round(float(np.percentile(lat_sorted, 50)), 2),
+                    "p99_ms": round(float(np.percentile(lat_sorted, 99)), 2),
+                    "max_rel_diff_vs_plain": max(rel(q["x"], p["x"]) for q, p in zip(served, plain))},
+    }
 
 
 # ------------------------------------------------------------------ oracle sample
@@ -352,6 +404,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", dest="forms", action="store_false",
+                    help="skip the batched / serving comparison")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -82,6 +82,29 @@ __device__ __forceinline__ double warp_sum_comp(float v) {
 }
 __device__ __forceinline__ double warp_sum_comp(double v) { return warp_sum(v); }
 
+// Double-float arithmetic on the FP32 pipe: (hi, lo) += (xh, xl) with the
+// rounding error of hi + xh recovered exactly (TwoSum) and carried in lo.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float xh, float xl) {
+  const float s = hi + xh;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (xh - bp);
+  lo = lo + xl + e;
+  hi = s;
+}
+
+// Kahan-compensated warp dot over strided elements, returned as (hi, lo).
+__device__ __forceinline__ float2 warp_df(float acc, float comp) {
+  // combine acc (with Kahan residue -comp) across the warp
+  float hi = acc, lo = -comp;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    df_add(hi, lo, h2, l2);
+  }
+  return make_float2(hi, lo);
+}
+
 // Block sum of NV per-thread partials (float or double); the result (double)
 // is valid in thread (0,0) only. `scratch` needs NV * 32 doubles. The warp
 // totals are combined by warp 0 with a fixed butterfly (no serial chain of

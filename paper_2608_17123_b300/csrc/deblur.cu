@@ -208,17 +208,29 @@ struct GcvBufs {
   double *gGA = nullptr, *gGD = nullptr, *ggA = nullptr, *ggD = nullptr, *gh = nullptr, *gwork = nullptr;
   double* gmdot_part = nullptr;
   double *gAd = nullptr, *gbA = nullptr, *gbD = nullptr, *gh2 = nullptr;
+  double* gtrt = nullptr;             // symbol traces on the first selection grid
+  size_t gwork_cap = 0;               // doubles in gwork
   float2* gpart2 = nullptr;
   size_t gpart2_cap = 0;
   int gkmax = 0;
   size_t gn = 0;
+  // Krylov basis K_k(A^T A, A^T b) of the projected GCV, kept between calls on
+  // the same level of the same solve (it depends on A and b only, not on the
+  // weights or the shift): columns V_0..V_{kc_cols-1} with their G_A and g_A
+  // entries, A^T b in gatb, the pending next direction in gt with its
+  // squared norm in gpend (device).
+  const void* kc_b = nullptr;
+  uint64_t kc_epoch = 0;
+  int kc_cols = 0;
+  double kc_bnorm2 = 0.0, kc_atb2 = 0.0;
+  double* gpend = nullptr;
 
   static size_t bytes(size_t n0, int kmax, int exact_max, int nsm) {
     size_t tot = n0 * sizeof(Acc) * (kmax + 9);
     tot += (size_t)kmax * kmax * sizeof(double) * 8 + (size_t)kmax * 4096 * sizeof(double);
     tot += (size_t)exact_max * exact_max * sizeof(double) + (size_t)kmax * 160 * sizeof(double);
     tot += (size_t)(2 * kmax + 4) * std::max<size_t>((n0 + 2047) / 2048, (size_t)4 * nsm) * 8;
-    return tot + 64 * 4096;
+    return tot + 64 * 4096 + 1024;
   }
 
   void alloc(Arena& A, size_t n0, int kmax, int exact_max, int nsm) {
@@ -233,11 +245,17 @@ struct GcvBufs {
     ggA = A.take<double>(kmax);
     ggD = A.take<double>(kmax);
     gh = A.take<double>(kmax);
-    gwork = A.take<double>((size_t)3 * kmax * kmax + (7 + 2 * SEL_MAXPTS + 8) * (size_t)kmax);
+    gwork_cap = (size_t)3 * kmax * kmax + (7 + 2 * SEL_MAXPTS + 8) * (size_t)kmax;
+    gwork = A.take<double>(gwork_cap);
     gAd = A.take<double>((size_t)std::max(exact_max, 1) * std::max(exact_max, 1));
     gbA = A.take<double>(kmax);
     gbD = A.take<double>(kmax);
     gh2 = A.take<double>(kmax);
+    gtrt = A.take<double>(SEL_MAXPTS);
+    gpend = A.take<double>(1);
+    kc_b = nullptr;
+    kc_epoch = 0;
+    kc_cols = 0;
     const size_t nch = std::max<size_t>((n0 + VCH_CHUNK - 1) / VCH_CHUNK, (size_t)4 * nsm);
     gpart2_cap = (size_t)(2 * kmax + 4) * nch;
     gpart2 = A.take<float2>(gpart2_cap);
@@ -271,15 +289,22 @@ struct Engine {
   double *gGA = nullptr, *gGD = nullptr, *ggA = nullptr, *ggD = nullptr, *gh = nullptr, *gwork = nullptr;
   double* gmdot_part = nullptr;
   double *gAd = nullptr, *gbA = nullptr, *gbD = nullptr, *gh2 = nullptr;
+  double* gtrt = nullptr;
+  size_t gwork_cap = 0;
   float2* gpart2 = nullptr;
   size_t gpart2_cap = 0;
   int gkmax = 0;
   size_t gn = 0;
 
-  void adopt(const GcvBufs<Acc>& b) {
+  GcvBufs<Acc>* gcur = nullptr;      // the buffers in use (for the Krylov cache)
+  GcvBufs<Acc> own_bufs;
+  uint64_t epoch = 0;                // unique per build (keys the Krylov cache)
+
+  void adopt(GcvBufs<Acc>& b) {
+    gcur = &b;
     gV = b.gV; gt = b.gt; gz = b.gz; gy = b.gy; gatb = b.gatb; gdtc = b.gdtc; gknext = b.gknext;
     gcx = b.gcx; gcy = b.gcy; gGA = b.gGA; gGD = b.gGD; ggA = b.ggA; ggD = b.ggD; gh = b.gh; gwork = b.gwork;
-    gmdot_part = b.gmdot_part; gAd = b.gAd; gbA = b.gbA; gbD = b.gbD; gh2 = b.gh2; gpart2 = b.gpart2;
+    gmdot_part = b.gmdot_part; gAd = b.gAd; gbA = b.gbA; gbD = b.gbD; gh2 = b.gh2; gtrt = b.gtrt; gwork_cap = b.gwork_cap; gpart2 = b.gpart2;
     gpart2_cap = b.gpart2_cap; gkmax = b.gkmax; gn = b.gn;
   }
 
@@ -310,6 +335,8 @@ struct Engine {
   void build(const double* psf_dev, int S, int m, int levels, db_wavelet wv, const double* b_dev, bool with_vectors,
              bool with_gcv = true) {
     Arena& A = arena ? *arena : ctx->arena;
+    static std::atomic<uint64_t> build_counter{0};
+    epoch = ++build_counter;
     H.S = S;
     H.levels = levels;
     H.lv.assign(levels, Level<T>());
@@ -425,9 +452,8 @@ struct Engine {
     CK(cudaMemsetAsync(d_cnt, 0, 64 * sizeof(unsigned), st));
     CK(cudaMemsetAsync(d_gb, 0, sizeof(GridBarrier), st));
     if (with_vectors && with_gcv) {
-      GcvBufs<Acc> b;
-      b.alloc(A, n0, kmax, go.exact_max_pixels, ctx->nsm);
-      adopt(b);
+      own_bufs.alloc(A, n0, kmax, go.exact_max_pixels, ctx->nsm);
+      adopt(own_bufs);
     }
   }
 
@@ -562,6 +588,41 @@ struct Engine {
     else CK(cudaMemsetAsync(ggD + j, 0, sizeof(double), st));
   }
 
+  // Selections (k_gcv_select, one block each, at most three) in one launch;
+  // in projected mode the symbol traces of the first grid (the same for all)
+  // come from one many-block pass (k_trace_table) beforehand. Returns gamma
+  // of each selection.
+  std::vector<double> select_multi(GcvSelectArgs* as, int na) {
+    REQUIRE(na >= 1 && na <= 3, "one to three selections per launch");
+    const GcvSelectArgs& f = as[0];
+    const double* tab = nullptr;
+    if (!f.exact && f.rho && f.npts >= 3) {
+      const int npts = std::min(f.npts, SEL_MAXPTS);
+      int nb = (int)std::min<size_t>(((size_t)f.npix + TRT_CHUNK - 1) / TRT_CHUNK, (size_t)2 * ctx->nsm);
+      nb = std::max(nb, 1);
+      if ((size_t)npts * nb <= gpart2_cap) {
+        { count_launch(); k_trace_table<<<nb, 256, 0, st>>>(f.rho, f.npix, f.s, f.lo, f.hi, npts, gpart2, d_cnt + 24,
+                                                            gtrt); }
+        CK(cudaGetLastError());
+        tab = gtrt;
+      }
+    }
+    int kmax = 0;
+    for (int i = 0; i < na; ++i) {
+      as[i].trace_tab = tab;
+      kmax = std::max(kmax, as[i].kk);
+    }
+    const size_t sm = sel_smem_bytes(kmax);
+    CK(cudaFuncSetAttribute(k_gcv_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    { count_launch(); k_gcv_select<<<na, SEL_THREADS, sm, st>>>(as[0], as[na > 1 ? 1 : 0], as[na > 2 ? 2 : 0]); }
+    CK(cudaGetLastError());
+    std::vector<double> g(na);
+    for (int i = 0; i < na; ++i) CK(cudaMemcpyAsync(&g[i], as[i].out, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return g;
+  }
+  double select(GcvSelectArgs a) { return select_multi(&a, 1)[0]; }
+
   double gcv(const Level<T>& L, int solver, bool weighted, bool shifted) {
     if (go.gamma_fixed > 0) return go.gamma_fixed;
     ctx->n_gcv.fetch_add(1, std::memory_order_relaxed);
@@ -571,12 +632,23 @@ struct Engine {
     const int gsz = grid_for(n, ctx->nsm);
     const T* wx = weighted ? L.a0x : nullptr;
     const T* wy = weighted ? L.a0y : nullptr;
-    // A^T b, ||b||^2
-    { count_launch(); k_to_acc<T, Acc><<<gsz, 256, 0, st>>>(n, L.b, (const T*)nullptr, gz); }
-    CK(cudaGetLastError());
-    const double bnorm2 = dot(n, gz, gz);
-    blur(L, true, gz, gatb);
-    const double atb2 = dot(n, gatb, gatb);
+    // A^T b, ||b||^2 (kept with the Krylov basis of the projected mode)
+    const bool fused = std::is_same<Acc, float>::value && (long long)n > (long long)go.exact_max_pixels;
+    const bool kc_hit = fused && gcur && gcur->kc_cols > 0 && gcur->kc_b == (const void*)L.b &&
+                        gcur->kc_epoch == epoch;
+    // every other path writes the buffers the cache lives in (G_A, A^T b)
+    if (!fused && gcur) { gcur->kc_b = nullptr; gcur->kc_cols = 0; }
+    double bnorm2, atb2;
+    if (kc_hit) {
+      bnorm2 = gcur->kc_bnorm2;
+      atb2 = gcur->kc_atb2;
+    } else {
+      { count_launch(); k_to_acc<T, Acc><<<gsz, 256, 0, st>>>(n, L.b, (const T*)nullptr, gz); }
+      CK(cudaGetLastError());
+      bnorm2 = dot(n, gz, gz);
+      blur(L, true, gz, gatb);
+      atb2 = dot(n, gatb, gatb);
+    }
     // D^T c
     bool has_c = false;
     if (shifted) {
@@ -603,33 +675,37 @@ struct Engine {
       { count_launch(); k_dense_blur<<<g2, 256, 0, st>>>(m, H.nterms, L.dlo, L.w, L.Bd_r, L.Bd_c, gAd); }
       { count_launch(); k_gram_dense<<<g2, 256, 0, st>>>(nn, gAd, gGA, ld); }
       { count_launch(); k_dense_DtD<T><<<g2, 256, 0, st>>>(m, wx, wy, gGD, ld); }
-      double bnorm2_e = bnorm2;
-      if (L.b64) {
-        // A^T b and ||b||^2 in double from the double right-hand side
-        { count_launch(); k_dense_matvecT<<<grid_for(n, ctx->nsm), 256, 0, st>>>(nn, gAd, L.b64, gbA); }
-        dot_dev<double>(n, L.b64, L.b64, d_box + 30);
-        CK(cudaMemcpyAsync(&bnorm2_e, d_box + 30, sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-      } else {
-        count_launch(); k_to_double<Acc><<<gsz, 256, 0, st>>>(n, gatb, gbA);
+      // A^T b, ||b||^2 and D^T c in double: the exact pencil of a tiny level is
+      // numerically singular and amplifies any rounding of these
+      const double* bd = L.b64;
+      if (!bd) {
+        { count_launch(); k_diff_to_double<T><<<gsz, 256, 0, st>>>(n, L.b, (const T*)nullptr, gh2); }
+        bd = gh2;
       }
-      if (has_c) { count_launch(); k_to_double<Acc><<<gsz, 256, 0, st>>>(n, gdtc, gbD); }
-      else CK(cudaMemsetAsync(gbD, 0, n * sizeof(double), st));
+      { count_launch(); k_dense_matvecT<<<grid_for(n, ctx->nsm), 256, 0, st>>>(nn, gAd, bd, gbA); }
+      dot_dev<double>(n, bd, bd, d_box + 30);
+      double bnorm2_e = 0.0;
+      CK(cudaMemcpyAsync(&bnorm2_e, d_box + 30, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (has_c) {
+        double* cxd = gmdot_part;
+        double* cyd = gmdot_part + n;
+        { count_launch(); k_diff_to_double<T><<<gsz, 256, 0, st>>>(n, L.a0x, solver == 2 ? L.a1x : nullptr, cxd); }
+        { count_launch(); k_diff_to_double<T><<<gsz, 256, 0, st>>>(n, L.a0y, solver == 2 ? L.a1y : nullptr, cyd); }
+        { count_launch(); k_Lt_w<double, T><<<gsz, 256, 0, st>>>(m, cxd, cyd, (const T*)nullptr, (const T*)nullptr, gbD); }
+      } else {
+        CK(cudaMemsetAsync(gbD, 0, n * sizeof(double), st));
+      }
       CK(cudaGetLastError());
       GcvSelectArgs a;
-      a.kk = nn; a.ld = ld; a.GA = gGA; a.GD = gGD; a.gA = gbA; a.gD = gbD;
+      a.kk = nn; a.ld = ld; a.GA = gGA; a.GD = gGD; a.gA = gbA; a.gD = gbD; a.kshift = -1;
       a.bnorm2 = bnorm2_e; a.n = (double)n; a.s = 1.0; a.rho = L.rho; a.npix = nn; a.exact = 1;
       a.lo = go.log10_gamma_lo; a.hi = go.log10_gamma_hi; a.tolx = go.refine_tol_log10;
       a.npts = go.grid_points; a.max_ext = 2; a.work = gwork; a.out = d_box + 24;
-      { count_launch(); k_gcv_select<<<1, SEL_THREADS, 0, st>>>(a); }
-      CK(cudaGetLastError());
-      double gamma_e = 0.0;
-      CK(cudaMemcpyAsync(&gamma_e, d_box + 24, sizeof(double), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      return gamma_e;
+      return select(a);
     }
     if constexpr (std::is_same<Acc, float>::value) {
-      return gcv_projected_fused(L, wx, wy, has_c, s, bnorm2, atb2);
+      return gcv_projected_fused(L, wx, wy, has_c, s, bnorm2, atb2, kc_hit);
     } else {
     // v_0 (double working precision: multi-launch path)
     CK(cudaMemcpyAsync(d_box + 20, &atb2, sizeof(double), cudaMemcpyHostToDevice, st));
@@ -694,14 +770,11 @@ struct Engine {
       }
       // small problem + selection
       GcvSelectArgs a;
-      a.kk = kk; a.ld = ld; a.GA = gGA; a.GD = gGD; a.gA = ggA; a.gD = ggD;
+      a.kk = kk; a.ld = ld; a.GA = gGA; a.GD = gGD; a.gA = ggA; a.gD = ggD; a.kshift = -1;
       a.bnorm2 = bnorm2; a.n = (double)n; a.s = s; a.rho = L.rho; a.npix = (int)n; a.exact = 0;
       a.lo = go.log10_gamma_lo; a.hi = go.log10_gamma_hi; a.tolx = go.refine_tol_log10;
       a.npts = go.grid_points; a.max_ext = 2; a.work = gwork; a.out = d_box + 24;
-      { count_launch(); k_gcv_select<<<1, SEL_THREADS, 0, st>>>(a); }
-      CK(cudaGetLastError());
-      CK(cudaMemcpyAsync(&gamma, d_box + 24, sizeof(double), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
+      gamma = select(a);
       if (gamma_prev > 0 && std::fabs(gamma - gamma_prev) <= 1e-3 * gamma_prev) return gamma;
       if (2 * kdim > kcap || kdim >= (int)n || broke) return gamma;
       gamma_prev = gamma;
@@ -723,10 +796,11 @@ struct Engine {
   }
 
   double gcv_projected_fused(const Level<T>& L, const T* wx, const T* wy, bool has_c, double s, double bnorm2,
-                             double atb2) {
+                             double atb2, bool kc_hit) {
     const size_t n = L.n;
     const int m = L.m;
     const int ld = gkmax;
+    GcvBufs<Acc>& C = *gcur;
     // chunk of E*256 elements per block, E chosen to give ~2 blocks per SM
     int E = VCH_E;
     while (E > 1 && (n + (size_t)E * VCH_THREADS - 1) / ((size_t)E * VCH_THREADS) < (size_t)2 * ctx->nsm) E >>= 1;
@@ -734,73 +808,110 @@ struct Engine {
     unsigned* cnt = d_cnt + 16;
     float* V = reinterpret_cast<float*>(gV);
     float* t = reinterpret_cast<float*>(gt);
-    // pending first direction: t = A^T b with ||t||^2 = atb2
-    CK(cudaMemcpyAsync(t, gatb, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(d_box + 21, &atb2, sizeof(double), cudaMemcpyHostToDevice, st));
-    const double dtc2 = has_c ? dot(n, gdtc, gdtc) : 0.0;
-    const int kcap = (int)std::min<size_t>((size_t)go.proj_dim_max, n);
-    int kdim = std::min<int>(go.proj_dim, kcap);
-    int cols = 0;
-    double gamma_prev = -1.0, gamma = 0.0;
-    for (;;) {
-      while (cols < kdim) {
-        const int j = cols;
-        // v_j = t / ||t|| (written by the A pass), z = A v_j, t = A^T z
-        blur_dev(L, false, gt, gz, d_box + 21, gV + (size_t)j * n);
-        blur_dev(L, true, gz, gt, nullptr, nullptr);
-        { count_launch(); k_gram_col<T><<<nch, VCH_THREADS, 0, st>>>(m, j, V, t, wx, wy,
-              reinterpret_cast<const float*>(gatb), has_c ? reinterpret_cast<const float*>(gdtc) : nullptr,
-              gpart2, cnt, gGA, gGD, ld, ggA, ggD, E); }
-        ++cols;
-        if (cols < kcap) {
-          // next direction: two classical Gram-Schmidt passes (the first reuses
-          // the Gram column G_A[i][j] = V_i . t)
-          { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, j + 1, V, n, gGA + j, ld, t,
-                VCH_UPDATE | VCH_DOTS, gpart2, cnt, gh, 1, nullptr, E); }
-          { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, j + 1, V, n, gh, 1, t,
-                VCH_UPDATE | VCH_NORM, gpart2, cnt, nullptr, 0, d_box + 21, E); }
-        }
-        CK(cudaGetLastError());
-      }
-      int kk = cols;
-      if (has_c) {
-        // shift direction orth(D^T c) in slot kk (two Gram-Schmidt passes)
-        float* vc = reinterpret_cast<float*>(gknext);
-        CK(cudaMemcpyAsync(vc, gdtc, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
-        { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, kk, V, n, nullptr, 0, vc, VCH_DOTS, gpart2, cnt,
-              gh, 1, nullptr, E); }
-        { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, kk, V, n, gh, 1, vc, VCH_UPDATE | VCH_DOTS, gpart2,
-              cnt, gh2, 1, nullptr, E); }
-        { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, kk, V, n, gh2, 1, vc, VCH_UPDATE | VCH_NORM,
-              gpart2, cnt, nullptr, 0, d_box + 22, E); }
-        CK(cudaGetLastError());
-        double nc2 = 0.0;
-        CK(cudaMemcpyAsync(&nc2, d_box + 22, sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (std::sqrt(nc2) > 1e-12 * std::sqrt(dtc2)) {
-          blur_dev(L, false, gknext, gz, d_box + 22, gV + (size_t)kk * n);
-          blur_dev(L, true, gz, gy, nullptr, nullptr);
-          { count_launch(); k_gram_col<T><<<nch, VCH_THREADS, 0, st>>>(m, kk, V, reinterpret_cast<float*>(gy), wx, wy,
-                reinterpret_cast<const float*>(gatb), reinterpret_cast<const float*>(gdtc), gpart2, cnt, gGA, gGD,
-                ld, ggA, ggD, E); }
-          CK(cudaGetLastError());
-          ++kk;
-        }
-      }
-      GcvSelectArgs a;
-      a.kk = kk; a.ld = ld; a.GA = gGA; a.GD = gGD; a.gA = ggA; a.gD = ggD;
-      a.bnorm2 = bnorm2; a.n = (double)n; a.s = s; a.rho = L.rho; a.npix = (int)n; a.exact = 0;
-      a.lo = go.log10_gamma_lo; a.hi = go.log10_gamma_hi; a.tolx = go.refine_tol_log10;
-      a.npts = go.grid_points; a.max_ext = 2; a.work = gwork; a.out = d_box + 24;
-      { count_launch(); k_gcv_select<<<1, SEL_THREADS, 0, st>>>(a); }
-      CK(cudaGetLastError());
-      CK(cudaMemcpyAsync(&gamma, d_box + 24, sizeof(double), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      if (gamma_prev > 0 && std::fabs(gamma - gamma_prev) <= 1e-3 * gamma_prev) return gamma;
-      if (2 * kdim > kcap || kdim >= (int)n) return gamma;
-      gamma_prev = gamma;
-      kdim *= 2;
+    const float* atbf = reinterpret_cast<const float*>(gatb);
+    const float* dtcf = has_c ? reinterpret_cast<const float*>(gdtc) : nullptr;
+    // the shift direction orth(D^T c) lives in the last slot of V and of the
+    // Gram matrices, so it never overwrites a cached Krylov column
+    const int kres = gkmax - 1;
+    if (!kc_hit) {
+      // start the basis: pending first direction t = A^T b with ||t||^2 = atb2
+      CK(cudaMemcpyAsync(t, gatb, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(C.gpend, &atb2, sizeof(double), cudaMemcpyHostToDevice, st));
+      C.kc_b = (const void*)L.b;
+      C.kc_epoch = epoch;
+      C.kc_cols = 0;
+      C.kc_bnorm2 = bnorm2;
+      C.kc_atb2 = atb2;
     }
+    const int cached = C.kc_cols;     // columns whose G_A, g_A are known; their G_D, g_D are stale
+    const double dtc2 = has_c ? dot(n, gdtc, gdtc) : 0.0;
+    const int kcap = (int)std::min<size_t>((size_t)std::min(go.proj_dim_max, kres - 2), n);
+    // the doubling sequence k = proj_dim, 2 proj_dim, ... (<= kcap); every
+    // selection of it runs in one launch and the rule is applied afterwards
+    // (the result is the one the sequential loop returns)
+    std::vector<int> seq;
+    for (int k = std::min<int>(go.proj_dim, kcap);; k *= 2) {
+      seq.push_back(k);
+      if (2 * k > kcap || k >= (int)n) break;
+    }
+    const int ktop = seq.back();
+    // G_D, g_D of cached columns for the current weights and shift
+    for (int j = 0; j < std::min(ktop, cached); ++j) {
+      count_launch();
+      k_gram_col<T><<<nch, VCH_THREADS, 0, st>>>(m, j, V + (size_t)j * n, j, V, nullptr, wx, wy, atbf, dtcf, gpart2,
+                                                 cnt, gGA, gGD, ld, ggA, ggD, E);
+    }
+    // new columns: v_j = t / ||t|| (written by the A pass), z = A v_j, t = A^T z
+    while (C.kc_cols < ktop) {
+      const int j = C.kc_cols;
+      blur_dev(L, false, gt, gz, C.gpend, gV + (size_t)j * n);
+      blur_dev(L, true, gz, gt, nullptr, nullptr);
+      { count_launch(); k_gram_col<T><<<nch, VCH_THREADS, 0, st>>>(m, j, V + (size_t)j * n, j, V, t, wx, wy, atbf,
+            dtcf, gpart2, cnt, gGA, gGD, ld, ggA, ggD, E); }
+      ++C.kc_cols;
+      if (C.kc_cols < kcap) {
+        // next direction: two classical Gram-Schmidt passes (the first reuses
+        // the Gram column G_A[i][j] = V_i . t)
+        { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, j + 1, V, n, gGA + j, ld, t,
+              VCH_UPDATE | VCH_DOTS, gpart2, cnt, gh, 1, nullptr, E); }
+        { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, j + 1, V, n, gh, 1, t,
+              VCH_UPDATE | VCH_NORM, gpart2, cnt, nullptr, 0, C.gpend, E); }
+      }
+      CK(cudaGetLastError());
+    }
+    // selections in groups of up to three per launch, the doubling rule
+    // (stop at the first dimension whose gamma agrees with the previous one
+    // to 0.1 %) applied in sequence order
+    double gamma = 0.0, prev = -1.0;
+    for (size_t g0 = 0; g0 < seq.size(); g0 += 3) {
+      const int ng = (int)std::min<size_t>(3, seq.size() - g0);
+      GcvSelectArgs args[3];
+      size_t woff = 0;
+      for (int bsel = 0; bsel < ng; ++bsel) {
+        const int kdim = seq[g0 + bsel];
+        const int kr = kres - bsel;       // slot of this selection's shift direction
+        int kk = kdim, kshift = -1;
+        if (has_c) {
+          // shift direction orth(D^T c) against V_0..V_{kdim-1} (two Gram-Schmidt passes)
+          float* vc = reinterpret_cast<float*>(gknext);
+          CK(cudaMemcpyAsync(vc, gdtc, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+          { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, kdim, V, n, nullptr, 0, vc, VCH_DOTS, gpart2,
+                cnt, gh, 1, nullptr, E); }
+          { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, kdim, V, n, gh, 1, vc, VCH_UPDATE | VCH_DOTS,
+                gpart2, cnt, gh2, 1, nullptr, E); }
+          { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, kdim, V, n, gh2, 1, vc, VCH_UPDATE | VCH_NORM,
+                gpart2, cnt, nullptr, 0, d_box + 22, E); }
+          CK(cudaGetLastError());
+          double nc2 = 0.0;
+          CK(cudaMemcpyAsync(&nc2, d_box + 22, sizeof(double), cudaMemcpyDeviceToHost, st));
+          CK(cudaStreamSynchronize(st));
+          if (std::sqrt(nc2) > 1e-12 * std::sqrt(dtc2)) {
+            float* vres = V + (size_t)kr * n;
+            blur_dev(L, false, gknext, gz, d_box + 22, gV + (size_t)kr * n);
+            blur_dev(L, true, gz, gy, nullptr, nullptr);
+            { count_launch(); k_gram_col<T><<<nch, VCH_THREADS, 0, st>>>(m, kdim, vres, kr, V,
+                  reinterpret_cast<float*>(gy), wx, wy, atbf, dtcf, gpart2, cnt, gGA, gGD, ld, ggA, ggD, E); }
+            CK(cudaGetLastError());
+            kk = kdim + 1;
+            kshift = kr;
+          }
+        }
+        GcvSelectArgs& a = args[bsel];
+        a.kk = kk; a.ld = ld; a.GA = gGA; a.GD = gGD; a.gA = ggA; a.gD = ggD; a.kshift = kshift;
+        a.bnorm2 = bnorm2; a.n = (double)n; a.s = s; a.rho = L.rho; a.npix = (int)n; a.exact = 0;
+        a.lo = go.log10_gamma_lo; a.hi = go.log10_gamma_hi; a.tolx = go.refine_tol_log10;
+        a.npts = go.grid_points; a.max_ext = 2; a.work = gwork + woff; a.out = d_box + 24 + 4 * bsel;
+        woff += sel_work_doubles(kk);
+      }
+      REQUIRE(woff <= gwork_cap, "GCV selection workspace too small");
+      const std::vector<double> gam = select_multi(args, ng);
+      for (int i = 0; i < ng; ++i) {
+        gamma = gam[i];
+        if (prev > 0 && std::fabs(gamma - prev) <= 1e-3 * prev) return gamma;
+        prev = gamma;
+      }
+    }
+    return gamma;
   }
 
   // ---------------------------------------------------------------- outer step
@@ -1035,7 +1146,10 @@ struct BatchSolver {
         CountScope cs(ctx);
         try {
           CK(cudaSetDevice(ctx->device));
-          for (size_t j = w; j < need.size(); j += nw) {
+          // problem p always goes to worker p % nw, so its GCV buffers (and
+          // the Krylov basis cached in them) are the ones it used last time
+          for (size_t j = 0; j < need.size(); ++j) {
+            if (need[j] % nw != w) continue;
             Prob& q = P[need[j]];
             const int kind = gcv_kind(q);
             q.E->adopt(gbufs[w]);

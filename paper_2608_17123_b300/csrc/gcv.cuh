@@ -141,29 +141,8 @@ __global__ void k_Lt_w(int m, const Acc* __restrict__ qx, const Acc* __restrict_
 
 // ---- fused Krylov-basis kernels ------------------------------------------------
 // Each block owns one contiguous chunk of the vectors; per-chunk partial sums
-// are kept as double-float pairs (float hi + float lo, error-free TwoSum) and
-// the block that finishes last adds the chunks in a fixed order.
-__device__ __forceinline__ void df_add(float& hi, float& lo, float xh, float xl) {
-  const float s = hi + xh;
-  const float bp = s - hi;
-  const float e = (hi - (s - bp)) + (xh - bp);
-  lo = lo + xl + e;
-  hi = s;
-}
-
-// Kahan-compensated warp dot over strided elements, returned as (hi, lo).
-__device__ __forceinline__ float2 warp_df(float acc, float comp) {
-  // combine acc (with Kahan residue -comp) across the warp
-  float hi = acc, lo = -comp;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-    df_add(hi, lo, h2, l2);
-  }
-  return make_float2(hi, lo);
-}
-
+// are kept as double-float pairs (float hi + float lo, error-free TwoSum, see
+// df_add) and the block that finishes last adds the chunks in a fixed order.
 constexpr int VCH_E = 8;                 // elements per thread per chunk
 constexpr int VCH_THREADS = 256;
 constexpr int VCH_CHUNK = VCH_E * VCH_THREADS;
@@ -253,14 +232,18 @@ __global__ void __launch_bounds__(VCH_THREADS) k_vchunk(size_t n, int nrows, con
   if (tid == 0) *cnt = 0;
 }
 
-// Gram column j: with y = L^T diag(w^2) L v_j (computed here),
-//   GA[i*ld + j] = V_i . t, GD[i*ld + j] = V_i . y (i <= j),
-//   gA[j] = atb . v_j, gD[j] = dtc . v_j (dtc may be null -> 0).
+// One Gram column for the basis vector vj against rows V_0..V_{nr-1} and
+// itself, stored as column jout (jout >= nr): with y = L^T diag(w^2) L vj
+// (computed here),
+//   GA[i*ld + jout] = V_i . t, GD[i*ld + jout] = V_i . y   (i < nr),
+//   GA[jout*ld + jout] = vj . t, GD[jout*ld + jout] = vj . y,
+//   gA[jout] = atb . vj, gD[jout] = dtc . vj (dtc may be null -> 0).
+// t == null computes only the D part (GD, gD), for a basis whose GA is known.
 template <typename T>
-__global__ void __launch_bounds__(VCH_THREADS) k_gram_col(int m, int j, const float* __restrict__ V,
-    const float* __restrict__ t, const T* __restrict__ wx, const T* __restrict__ wy, const float* __restrict__ atb,
-    const float* __restrict__ dtc, float2* __restrict__ part, unsigned* cnt, double* GA, double* GD, int ld,
-    double* gA, double* gD, int E) {
+__global__ void __launch_bounds__(VCH_THREADS) k_gram_col(int m, int nr, const float* __restrict__ vj, int jout,
+    const float* __restrict__ V, const float* __restrict__ t, const T* __restrict__ wx, const T* __restrict__ wy,
+    const float* __restrict__ atb, const float* __restrict__ dtc, float2* __restrict__ part, unsigned* cnt,
+    double* GA, double* GD, int ld, double* gA, double* gD, int E) {
   __shared__ float ts[VCH_CHUNK];
   __shared__ float ys[VCH_CHUNK];
   __shared__ int s_last;
@@ -269,13 +252,13 @@ __global__ void __launch_bounds__(VCH_THREADS) k_gram_col(int m, int j, const fl
   const int CH = E * VCH_THREADS;
   const size_t beg = (size_t)ch * CH;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = VCH_THREADS / 32;
-  const float* vj = V + (size_t)j * n;
+  const bool with_a = (t != nullptr);
   for (int k = 0; k < E; ++k) {
     const int le = k * VCH_THREADS + tid;
     const size_t i = beg + le;
     float tv = 0.f, yv = 0.f;
     if (i < n) {
-      tv = t[i];
+      if (with_a) tv = t[i];
       const int r = (int)(i % m), c = (int)(i / m);
       const float xv = vj[i];
       auto W = [&](const T* p, size_t q) -> float { return p ? (float)to_acc(p[q]) : 1.f; };
@@ -288,15 +271,16 @@ __global__ void __launch_bounds__(VCH_THREADS) k_gram_col(int m, int j, const fl
     ys[le] = yv;
   }
   __syncthreads();
-  const int nrows = j + 1;
-  // rows 0..j: two dots each (slots 2i, 2i+1); row j+1: atb.v_j and dtc.v_j
+  const int nrows = nr + 1;            // rows V_0..V_{nr-1} and vj itself
+  // rows 0..nr: two dots each (slots 2i, 2i+1); row nr+1: atb.vj and dtc.vj
   for (int i = wid; i <= nrows; i += nw) {
     float a1 = 0.f, c1 = 0.f, a2 = 0.f, c2 = 0.f;
+    const float* vi = i < nr ? V + (size_t)i * n : vj;
     for (int le = lane; le < CH; le += 32) {
       if (beg + le >= n) break;
       float p1, q1, p2, q2;
-      if (i < nrows) { const float vv = V[(size_t)i * n + beg + le]; p1 = vv; q1 = ts[le]; p2 = vv; q2 = ys[le]; }
-      else { const float vv = vj[beg + le]; p1 = atb[beg + le]; q1 = vv; p2 = dtc ? dtc[beg + le] : 0.f; q2 = vv; }
+      if (i < nrows) { const float vv = vi[beg + le]; p1 = vv; q1 = ts[le]; p2 = vv; q2 = ys[le]; }
+      else { const float vv = vj[beg + le]; p1 = with_a ? atb[beg + le] : 0.f; q1 = vv; p2 = dtc ? dtc[beg + le] : 0.f; q2 = vv; }
       float y = p1 * q1 - c1, tt = a1 + y; c1 = (tt - a1) - y; a1 = tt;
       y = p2 * q2 - c2; tt = a2 + y; c2 = (tt - a2) - y; a2 = tt;
     }
@@ -315,17 +299,20 @@ __global__ void __launch_bounds__(VCH_THREADS) k_gram_col(int m, int j, const fl
   __syncthreads();
   if (!s_last) return;
   for (int sidx = tid; sidx < 2 * (nrows + 1); sidx += VCH_THREADS) {
+    const int i = sidx >> 1;
+    const bool a_part = (sidx & 1) == 0;
+    if (a_part && !with_a) continue;
     float hi = 0.f, lo = 0.f;
     for (int c = 0; c < nch; ++c) {
       const float2 pv = __ldcg(&part[(size_t)sidx * nch + c]);
       df_add(hi, lo, pv.x, pv.y);
     }
     const double v = (double)hi + (double)lo;
-    const int i = sidx >> 1;
     if (i < nrows) {
-      if ((sidx & 1) == 0) GA[(size_t)i * ld + j] = v; else GD[(size_t)i * ld + j] = v;
+      const int row = i < nr ? i : jout;
+      if (a_part) GA[(size_t)row * ld + jout] = v; else GD[(size_t)row * ld + jout] = v;
     } else {
-      if ((sidx & 1) == 0) gA[j] = v; else gD[j] = v;
+      if (a_part) gA[jout] = v; else gD[jout] = v;
     }
   }
   if (tid == 0) *cnt = 0;
@@ -394,6 +381,13 @@ __global__ void k_dense_matvecT(int n, const double* __restrict__ Ad, const doub
   }
 }
 
+// y = a - b (b may be null) in double, from storage-precision inputs.
+template <typename T>
+__global__ void k_diff_to_double(size_t n, const T* __restrict__ a, const T* __restrict__ b, double* __restrict__ y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (double)to_acc(a[i]) - (b ? (double)to_acc(b[i]) : 0.0);
+}
+
 template <typename Acc>
 __global__ void k_to_double(size_t n, const Acc* __restrict__ x, double* __restrict__ y) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -405,11 +399,19 @@ __global__ void k_to_double(size_t n, const Acc* __restrict__ x, double* __restr
 // (Householder, T tridiagonal) and p_A = Q^T R^{-1} g_A, p_D = Q^T R^{-1} g_D,
 // the trial solution of (G_A + gamma G_D) y = g_A + gamma g_D is
 // y = R^{-T} Q w with ((1 - gamma) T + gamma I) w = p_A + gamma p_D (a
-// tridiagonal SPD system, one Thomas sweep per gamma); the residual is
-// evaluated without cancellation as gamma^2 u^T T u + r0^2 (sel_numerator).
-// The trace is either the symbol trace (projected mode) or, when the basis is
-// the whole space (exact mode, tiny levels), sum_j lam_j / (lam_j + gamma (1 - lam_j))
-// over the eigenvalues of T (bisection with Sturm counts).
+// tridiagonal SPD system per gamma, one Thomas sweep); the residual is
+// evaluated without cancellation as gamma^2 u^T T u + r0^2. The trace is either the symbol
+// trace (projected mode) or, when the basis is the whole space (exact mode,
+// tiny levels), sum_j lam_j / (lam_j + gamma (1 - lam_j)) over the
+// eigenvalues of T (bisection with Sturm counts).
+//
+// Layout: the k x k working matrix (M, then R, then C and the reduction to
+// T) lives in shared memory when k <= SEL_SMEM_K (row pitch k|1, so a warp
+// reading a column, or the same column index of consecutive rows, touches
+// distinct banks); the two k x k intermediates of the congruence go to the
+// global work buffer. FP64 costs ~64 cycles of pipe time per warp
+// instruction on this part, so reductions run only in the warps that hold
+// data and the tridiagonalisation updates the lower triangle only.
 struct GcvSelectArgs {
   int kk;                 // basis dimension
   int ld;                 // leading dimension of GA, GD
@@ -425,11 +427,30 @@ struct GcvSelectArgs {
   int exact;              // 1: trace from the eigenvalues of T
   double lo, hi, tolx;
   int npts, max_ext;
-  double* work;           // >= 3 kk*kk + (6 + 2*SEL_MAXPTS + 1) kk doubles
+  const double* trace_tab;  // projected mode: traces on the first grid (npts values), or null
+  int kshift;             // >= 0: basis vector kk-1 is stored at row/column kshift of GA, GD, gA, gD
+  double* work;           // >= sel_work_doubles(kk)
   double* out;            // out[0] = gamma, out[1] = extensions, out[2] = GCV value
 };
 
 constexpr int SEL_THREADS = 512;
+constexpr int SEL_MAXPTS = 64;
+constexpr int SEL_SMEM_K = 162;   // largest basis whose matrix is kept in shared memory
+constexpr int SEL_NVEC = 10;      // k-vectors in shared memory
+
+__host__ __device__ inline int sel_lds(int kk) { return kk | 1; }
+// Global work of one selection: (matrix if not in shared memory), X, C, and
+// the per-grid-point Thomas scratch.
+inline size_t sel_work_doubles(int kk) {
+  return (kk <= SEL_SMEM_K ? 0 : (size_t)kk * sel_lds(kk)) + (size_t)2 * kk * kk + (size_t)2 * SEL_MAXPTS * kk;
+}
+// Dynamic shared memory of k_gcv_select: the k-vectors, then (k <= SEL_SMEM_K)
+// the working matrix.
+inline size_t sel_smem_bytes(int kk) {
+  size_t v = (size_t)SEL_NVEC * kk * sizeof(double);
+  if (kk <= SEL_SMEM_K) v += (size_t)kk * sel_lds(kk) * sizeof(double);
+  return v;
+}
 
 // 1/x in double from a float reciprocal refined by two Newton steps
 // (22 -> 44 -> 88 bits, i.e. correctly rounded to within an ulp); an FP64
@@ -442,27 +463,56 @@ __device__ __forceinline__ double rcp_d(double x) {
   y = y * (2.0 - x * y);
   return y;
 }
-constexpr int SEL_MAXPTS = 64;
+
+// 1/sqrt(x) in double: float estimate, then two Newton steps
+// y <- y (3 - x y^2) / 2 (each roughly doubles the correct bits).
+__device__ __forceinline__ double rsqrt_d(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x > 1e-300 ? x : 1e-300);
+  double y = (double)rsqrtf((float)x);
+  y = y * (1.5 - 0.5 * x * y * y);
+  y = y * (1.5 - 0.5 * x * y * y);
+  return y;
+}
+
+// Block sum of N doubles held by threads [0, nact); the other threads pass
+// zeros and skip the FP64 shuffles. Result in every thread. sh >= 32 N.
+template <int N>
+__device__ __forceinline__ void sel_sumN(double (&v)[N], int nact, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (nact + 31) >> 5;
+  if (wid < nw) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = warp_sum(v[k]);
+  }
+  __syncthreads();
+  if (lane == 0 && wid < nw) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) sh[k * 32 + wid] = v[k];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      double t = lane < nw ? sh[k * 32 + lane] : 0.0;
+      t = warp_sum(t);
+      if (lane == 0) sh[k * 32] = t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < N; ++k) v[k] = sh[k * 32];
+  __syncthreads();
+}
 
 __device__ double sel_block_sum(double v, double* sh) {
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  double s = (threadIdx.x < 32 && threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-  if (threadIdx.x < 32) s = warp_sum(s);
-  __syncthreads();
-  if (threadIdx.x == 0) sh[0] = s;
-  __syncthreads();
-  double r = sh[0];
-  __syncthreads();
-  return r;
+  double t[1] = {v};
+  sel_sumN<1>(t, blockDim.x, sh);
+  return t[0];
 }
 
 // Solve ((1 - gamma) T + gamma I) u = f by one Thomas sweep (T symmetric
 // tridiagonal: diagonal d, off-diagonal e; the matrix is SPD for gamma > 0
-// and for gamma = 0 when T is). cw is scratch of length kk.
+// and for gamma = 0 when T is). cw is scratch of length kk. One thread.
 __device__ void sel_tri_solve(int kk, const double* d, const double* e, const double* f, double gamma,
                               double* cw, double* u, double shift = 0.0) {
   const double a = 1.0 - gamma;
@@ -498,196 +548,459 @@ __device__ double sel_numerator(int kk, const double* d, const double* e, const 
   return gamma * gamma * q + r02;
 }
 
+// 2^(-e) with e the binary exponent of x (x finite, nonzero): multiplying by
+// it is exact and brings |x| into [0.5, 1).
+__device__ __forceinline__ double exp2_neg_exponent(double x) {
+  const long long bits = __double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7ff) - 1022;
+  return __longlong_as_double((long long)(1023 - e) << 52);
+}
+
+// Numerator gamma^2 u^T T u + r0^2 with ((1-gamma) T + gamma I) u = f, by
+// the LDL^T elimination written through the leading minors
+//   D_i = b_i D_{i-1} - a_i^2 D_{i-2},  pivot_i = D_i / D_{i-1},
+// so the sequential recurrences carry one or two FP64 operations per row and
+// every reciprocal is taken in parallel afterwards (a single thread issuing
+// FP64 costs ~64 cycles per instruction here, whatever the dependencies).
+// (D_i, D_{i-1}) are rescaled together by a power of two every 4 rows, which
+// leaves the pivots unchanged. The elimination and its subtractions are those
+// of a Thomas sweep. Warp 0 runs the recurrences while warps 1.. sum the
+// symbol trace (projected mode); all threads call it. wk: 3 kk doubles.
+__device__ double sel_eval(const GcvSelectArgs& a, int kk, const double* dg, const double* eo, const double* f,
+                           double r02, const double* lam, double gamma, double* u, double* wk, double* sh,
+                           double* tr_out) {
+  double* Dv = wk;            // D_i, then alpha_i = f_i / pivot_i
+  double* Dp = wk + kk;       // D_{i-1} (same scaling), then beta_i = a_i / pivot_i
+  double* cw = wk + 2 * kk;   // a_{i+1} / pivot_i
+  const double g1 = 1.0 - gamma, g0 = gamma;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  __shared__ double s_trp[32];
+  // (1) leading minors (thread 0) || trace partial sums (warps 1..)
+  if (tid == 0) {
+    double dm1 = 1.0, dm2 = 0.0;
+    for (int i = 0; i < kk; ++i) {
+      const double ai = i > 0 ? g1 * eo[i - 1] : 0.0;
+      const double di = (g1 * dg[i] + g0) * dm1 - (ai * ai) * dm2;
+      Dv[i] = di;
+      Dp[i] = dm1;
+      dm2 = dm1;
+      dm1 = di;
+      if ((i & 3) == 3 && di != 0.0) {
+        const double sc = exp2_neg_exponent(di);
+        dm1 *= sc;
+        dm2 *= sc;
+      }
+    }
+  }
+  double trp = 0.0;
+  if (wid > 0) {
+    if (a.exact) {
+      for (int j = tid - 32; j < kk; j += blockDim.x - 32) trp += lam[j] / (lam[j] + gamma * (1.0 - lam[j]));
+    } else {
+      const float gs = (float)(gamma * a.s);
+      float sum = 0.f, comp = 0.f;
+      constexpr int B = 8;
+      const int nt = blockDim.x - 32;
+      for (int base = tid - 32; base < a.npix; base += nt * B) {
+        float r[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+          const int i = base + q * nt;
+          r[q] = i < a.npix ? __ldg(a.rho + i) : -1.f;
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+          if (r[q] < 0.f) continue;
+          const float term = __frcp_rn(1.0f + gs * r[q]);
+          const float y = term - comp;
+          const float t = sum + y;
+          comp = (t - sum) - y;
+          sum = t;
+        }
+      }
+      trp = (double)sum - (double)comp;
+    }
+    trp = warp_sum(trp);
+    if (lane == 0) s_trp[wid] = trp;
+  }
+  __syncthreads();
+  // (2) reciprocals of the pivots, in parallel
+  for (int i = tid; i < kk; i += blockDim.x) {
+    const double d = Dv[i];
+    const double inv = d != 0.0 ? Dp[i] * rcp_d(d) : 0.0;
+    const double ai = i > 0 ? g1 * eo[i - 1] : 0.0;
+    const double ci = i + 1 < kk ? g1 * eo[i] : 0.0;
+    Dv[i] = f[i] * inv;
+    Dp[i] = ai * inv;
+    cw[i] = ci * inv;
+  }
+  __syncthreads();
+  // (3) forward and back substitution (thread 0); trace total (warp 1)
+  if (tid == 0) {
+    double y = Dv[0];
+    u[0] = y;
+    for (int i = 1; i < kk; ++i) {
+      y = Dv[i] - Dp[i] * y;
+      u[i] = y;
+    }
+    double un = u[kk - 1];
+    for (int i = kk - 2; i >= 0; --i) {
+      un = u[i] - cw[i] * un;
+      u[i] = un;
+    }
+  } else if (wid == 1) {
+    const int nw = blockDim.x >> 5;
+    double t = (lane >= 1 && lane < nw) ? s_trp[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) *tr_out = t;
+  }
+  __syncthreads();
+  // (4) u^T T u
+  double q[1] = {0.0};
+  for (int i = tid; i < kk; i += blockDim.x) {
+    double tu = dg[i] * u[i];
+    if (i > 0) tu += eo[i - 1] * u[i - 1];
+    if (i + 1 < kk) tu += eo[i] * u[i + 1];
+    q[0] += u[i] * tu;
+  }
+  sel_sumN<1>(q, kk, sh);
+  return gamma * gamma * q[0] + r02;
+}
+
+// Symbol trace sum_i 1 / (1 + gamma s rho_i) for one gamma (all threads;
+// loads in batches of 8 per thread, Kahan-compensated float sums).
+__device__ double sel_trace_one(const GcvSelectArgs& a, double gamma, double* sh) {
+  const float gs = (float)(gamma * a.s);
+  float sum = 0.f, comp = 0.f;
+  constexpr int B = 8;
+  for (int base = threadIdx.x; base < a.npix; base += blockDim.x * B) {
+    float r[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      const int i = base + q * blockDim.x;
+      r[q] = i < a.npix ? __ldg(a.rho + i) : -1.f;
+    }
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      if (r[q] < 0.f) continue;
+      const float term = __frcp_rn(1.0f + gs * r[q]);
+      const float y = term - comp;
+      const float t = sum + y;
+      comp = (t - sum) - y;
+      sum = t;
+    }
+  }
+  return sel_block_sum((double)sum - (double)comp, sh);
+}
+
 // Trace term for a set of gammas (all threads); returns per-gamma traces in tr[].
 __device__ void sel_traces(const GcvSelectArgs& a, const double* lam, int ng, const double* gam, double* tr,
                            double* sh) {
   for (int g = 0; g < ng; ++g) {
-    double part = 0.0;
     if (a.exact) {
+      double part = 0.0;
       for (int j = threadIdx.x; j < a.kk; j += blockDim.x) {
         const double l = lam[j];
         part += l / (l + gam[g] * (1.0 - l));
       }
+      const double t = sel_block_sum(part, sh);
+      if (threadIdx.x == 0) tr[g] = t;
     } else {
-      const float gs = (float)(gam[g] * a.s);
-      float sum = 0.f, comp = 0.f;
-      for (int i = threadIdx.x; i < a.npix; i += blockDim.x) {
-        const float term = __frcp_rn(1.0f + gs * a.rho[i]);
-        const float y = term - comp;
-        const float t = sum + y;
-        comp = (t - sum) - y;
-        sum = t;
-      }
-      part = (double)sum - (double)comp;
+      const double t = sel_trace_one(a, gam[g], sh);
+      if (threadIdx.x == 0) tr[g] = t;
     }
-    tr[g] = sel_block_sum(part, sh);
   }
+  __syncthreads();
 }
 
-__global__ void __launch_bounds__(SEL_THREADS) k_gcv_select(GcvSelectArgs a) {
-  __shared__ double sh[64];
+// Symbol traces on the first selection grid (npts log-spaced gammas on
+// [lo, hi], the same points as k_gcv_select) in one pass over rho by many
+// blocks: each block takes a chunk of pixels into shared memory and every
+// thread sums its gammas over the chunk (Kahan); block partials as (hi, lo)
+// float pairs, combined in a fixed order by the last block.
+constexpr int TRT_CHUNK = 4096;
+__global__ void __launch_bounds__(256) k_trace_table(const float* __restrict__ rho, int npix, double s, double lo,
+                                                     double hi, int npts, float2* part, unsigned* cnt,
+                                                     double* tab) {
+  __shared__ float sr[TRT_CHUNK];
+  __shared__ int s_last;
+  const int nb = gridDim.x;
+  const double step = (hi - lo) / (npts - 1);
+  float sum[SEL_MAXPTS / 32 + 1], comp[SEL_MAXPTS / 32 + 1];
+  float gs[SEL_MAXPTS / 32 + 1];
+  constexpr int G = SEL_MAXPTS / 32 + 1;
+  // thread t handles gammas t % 32 + 32 q (lanes of a warp cover the gammas;
+  // warps split the chunk)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < G; ++q) {
+    sum[q] = comp[q] = 0.f;
+    const int j = lane + 32 * q;
+    gs[q] = j < npts ? (float)(pow(10.0, (j == npts - 1) ? hi : lo + j * step) * s) : 0.f;
+  }
+  for (int ch = blockIdx.x; ch * TRT_CHUNK < npix; ch += nb) {
+    const int beg = ch * TRT_CHUNK;
+    const int len = min(TRT_CHUNK, npix - beg);
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) sr[i] = rho[beg + i];
+    __syncthreads();
+    for (int i = wid; i < len; i += nw) {
+      const float r = sr[i];
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        const float term = __frcp_rn(1.0f + gs[q] * r);
+        const float y = term - comp[q];
+        const float t = sum[q] + y;
+        comp[q] = (t - sum[q]) - y;
+        sum[q] = t;
+      }
+    }
+  }
+  // per-gamma block partial: combine the warps' (sum, -comp) pairs
+  __shared__ float2 sw[8][SEL_MAXPTS + 32];
+#pragma unroll
+  for (int q = 0; q < G; ++q) sw[wid][lane + 32 * q] = make_float2(sum[q], -comp[q]);
+  __syncthreads();
+  for (int j = threadIdx.x; j < npts; j += blockDim.x) {
+    float h = 0.f, l = 0.f;
+    for (int w = 0; w < nw; ++w) df_add(h, l, sw[w][j].x, sw[w][j].y);
+    part[(size_t)j * nb + blockIdx.x] = make_float2(h, l);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(cnt, 1u) == (unsigned)nb - 1);
+    __threadfence();
+  }
+  __syncthreads();
+  if (!s_last) return;
+  for (int j = threadIdx.x; j < npts; j += blockDim.x) {
+    float h = 0.f, l = 0.f;
+    for (int b = 0; b < nb; ++b) {
+      const float2 pv = __ldcg(&part[(size_t)j * nb + b]);
+      df_add(h, l, pv.x, pv.y);
+    }
+    tab[j] = (double)h + (double)l;
+  }
+  if (threadIdx.x == 0) *cnt = 0;
+}
+
+// Up to three independent selections (different basis dimensions of one GCV
+// call) in one launch, one block each.
+__global__ void __launch_bounds__(SEL_THREADS) k_gcv_select(GcvSelectArgs a0, GcvSelectArgs a1, GcvSelectArgs a2) {
+  GcvSelectArgs a = a0;
+  if (blockIdx.x == 1) a = a1;
+  else if (blockIdx.x == 2) a = a2;
+  extern __shared__ __align__(16) double sdyn[];
+  __shared__ double sh[32 * 3];
   __shared__ double s_gam[SEL_MAXPTS], s_tr[SEL_MAXPTS], s_f[SEL_MAXPTS];
+  __shared__ double s_bc[4];
   const int kk = a.kk, ld = a.ld, tid = threadIdx.x, nth = blockDim.x;
-  double* M = a.work;                 // kk x kk (row-major M[i*kk + j])
-  double* C = M + kk * kk;            // kk x kk
-  double* X = C + kk * kk;            // kk x kk
-  double* pA = X + kk * kk;
+  const int lds = sel_lds(kk);
+  const bool in_smem = kk <= SEL_SMEM_K;
+  double* pA = sdyn;
   double* pD = pA + kk;
   double* dg = pD + kk;               // tridiagonal diagonal
   double* eo = dg + kk;               // tridiagonal off-diagonal
-  double* lam = eo + kk;              // eigenvalues of T (exact mode)
-  double* scratch = lam + 2 * kk;     // per-thread Thomas scratch for the grid: SEL_MAXPTS * 2 kk
-  auto GAe = [&](int i, int j) { return i <= j ? a.GA[(size_t)i * ld + j] : a.GA[(size_t)j * ld + i]; };
-  auto GDe = [&](int i, int j) { return i <= j ? a.GD[(size_t)i * ld + j] : a.GD[(size_t)j * ld + i]; };
-  // 1. M = G_A + G_D, C = G_A (full symmetric)
-  for (int idx = tid; idx < kk * kk; idx += nth) {
-    int i = idx / kk, j = idx % kk;
-    M[idx] = GAe(i, j) + GDe(i, j);
-    C[idx] = GAe(i, j);
-  }
+  double* u = eo + kk;
+  double* p = u + kk;
+  double* colc = p + kk;
+  double* rdiag = colc + kk;
+  double* fvec = rdiag + kk;
+  double* lam = fvec + kk;            // eigenvalues of T (exact mode)
+  double* S = in_smem ? sdyn + SEL_NVEC * kk : a.work;          // working matrix, pitch lds
+  double* X = in_smem ? a.work : a.work + (size_t)kk * lds;     // R^{-1} G_A (global)
+  double* Cg = X + (size_t)kk * kk;                             // R^{-1} G_A R^{-T} (global)
+  double* scratch = Cg + (size_t)kk * kk;                       // grid Thomas scratch, 2 kk per point
+  auto mapk = [&](int i) { return (a.kshift >= 0 && i == kk - 1) ? a.kshift : i; };
+  auto GAe = [&](int i, int j) {
+    i = mapk(i); j = mapk(j);
+    return i <= j ? a.GA[(size_t)i * ld + j] : a.GA[(size_t)j * ld + i];
+  };
+  auto GDe = [&](int i, int j) {
+    i = mapk(i); j = mapk(j);
+    return i <= j ? a.GD[(size_t)i * ld + j] : a.GD[(size_t)j * ld + i];
+  };
+  // 1. S = M = G_A + G_D (lower triangle), p_A = g_A, p_D = g_D
+  // (element loops run one row per warp, lanes over the columns: no integer
+  // division per element)
+  const int lane = tid & 31, wid = tid >> 5, nwarp = nth >> 5;
+  for (int i = wid; i < kk; i += nwarp)
+    for (int j = lane; j <= i; j += 32) S[i * lds + j] = GAe(i, j) + GDe(i, j);
+  for (int i = tid; i < kk; i += nth) { pA[i] = a.gA[mapk(i)]; pD[i] = a.gD[mapk(i)]; }
   __syncthreads();
-  __shared__ double s_md;
   if (tid == 0) {
     double md = 0.0;
-    for (int i = 0; i < kk; ++i) md = fmax(md, M[i * kk + i]);
-    s_md = md;
+    for (int i = 0; i < kk; ++i) md = fmax(md, S[i * lds + i]);
+    s_bc[0] = md;
   }
   __syncthreads();
-  const double md = s_md;
-  const double piv_floor = 1e-14 * md;
+  const double piv_floor = 1e-14 * s_bc[0];
   // 2. Cholesky M = R R^T (lower, in place); rdiag = 1 / diag(R)
-  double* rdiag = lam + kk;           // kk entries before the Thomas scratch
-  __shared__ double s_rc;
   for (int c = 0; c < kk; ++c) {
     if (tid == 0) {
-      const double piv = M[c * kk + c];
-      const double r = sqrt(piv > piv_floor ? piv : piv_floor);
-      M[c * kk + c] = r;
-      s_rc = 1.0 / r;
-      rdiag[c] = s_rc;
+      const double piv = S[c * lds + c];
+      const double pv = piv > piv_floor ? piv : piv_floor;
+      const double ir = rsqrt_d(pv);
+      S[c * lds + c] = pv * ir;
+      rdiag[c] = ir;
     }
     __syncthreads();
-    const double rc = s_rc;
-    for (int i = c + 1 + tid; i < kk; i += nth) M[i * kk + c] *= rc;
+    const double ir = rdiag[c];
+    for (int i = c + 1 + tid; i < kk; i += nth) {
+      const double v = S[i * lds + c] * ir;
+      S[i * lds + c] = v;
+      colc[i] = v;
+    }
     __syncthreads();
-    const int rem = kk - c - 1;
-    for (int idx = tid; idx < rem * rem; idx += nth) {
-      const int i = c + 1 + idx / rem, j = c + 1 + idx % rem;
-      if (j <= i) M[i * kk + j] -= M[i * kk + c] * M[j * kk + c];
+    for (int i = c + 1 + wid; i < kk; i += nwarp) {
+      const double ci = colc[i];
+      double* Si = S + (size_t)i * lds;
+      for (int j = c + 1 + lane; j <= i; j += 32) Si[j] -= ci * colc[j];
     }
     __syncthreads();
   }
-  // 3. X = R^{-1} G_A, pA = R^{-1} g_A, pD = R^{-1} g_D (one column per thread,
-  //    four partial sums to shorten the dependent chain)
+  // 3. X = R^{-1} G_A, p_A <- R^{-1} p_A, p_D <- R^{-1} p_D (one column per
+  //    thread, eight partial sums to shorten the dependent chain)
   for (int q = tid; q < kk + 2; q += nth) {
+    double* vcol = q == kk ? pA : pD;
     for (int i = 0; i < kk; ++i) {
-      double s0 = q < kk ? C[i * kk + q] : (q == kk ? a.gA[i] : a.gD[i]);
-      double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      double sacc[8];
+      sacc[0] = q < kk ? GAe(i, q) : vcol[i];
+#pragma unroll
+      for (int r = 1; r < 8; ++r) sacc[r] = 0.0;
+      const double* Ri = S + (size_t)i * lds;
       int l = 0;
-      for (; l + 3 < i; l += 4) {
-        const double x0 = q < kk ? X[l * kk + q] : (q == kk ? pA[l] : pD[l]);
-        const double x1 = q < kk ? X[(l + 1) * kk + q] : (q == kk ? pA[l + 1] : pD[l + 1]);
-        const double x2 = q < kk ? X[(l + 2) * kk + q] : (q == kk ? pA[l + 2] : pD[l + 2]);
-        const double x3 = q < kk ? X[(l + 3) * kk + q] : (q == kk ? pA[l + 3] : pD[l + 3]);
-        s0 -= M[i * kk + l] * x0; s1 -= M[i * kk + l + 1] * x1;
-        s2 -= M[i * kk + l + 2] * x2; s3 -= M[i * kk + l + 3] * x3;
+      if (q < kk) {
+        for (; l + 7 < i; l += 8) {
+#pragma unroll
+          for (int r = 0; r < 8; ++r) sacc[r] -= Ri[l + r] * X[(size_t)(l + r) * kk + q];
+        }
+        for (; l < i; ++l) sacc[0] -= Ri[l] * X[(size_t)l * kk + q];
+      } else {
+        for (; l + 7 < i; l += 8) {
+#pragma unroll
+          for (int r = 0; r < 8; ++r) sacc[r] -= Ri[l + r] * vcol[l + r];
+        }
+        for (; l < i; ++l) sacc[0] -= Ri[l] * vcol[l];
       }
-      for (; l < i; ++l) s0 -= M[i * kk + l] * (q < kk ? X[l * kk + q] : (q == kk ? pA[l] : pD[l]));
-      const double v = ((s0 + s1) + (s2 + s3)) * rdiag[i];
-      if (q < kk) X[i * kk + q] = v; else if (q == kk) pA[i] = v; else pD[i] = v;
+      const double v = (((sacc[0] + sacc[1]) + (sacc[2] + sacc[3])) + ((sacc[4] + sacc[5]) + (sacc[6] + sacc[7]))) *
+                       rdiag[i];
+      if (q < kk) X[(size_t)i * kk + q] = v; else vcol[i] = v;
     }
   }
   __syncthreads();
-  // 4. C = R^{-1} X^T  (= R^{-1} G_A R^{-T})
+  // 4. C = R^{-1} X^T (= R^{-1} G_A R^{-T}), column q per thread
   for (int q = tid; q < kk; q += nth) {
     for (int i = 0; i < kk; ++i) {
-      double s0 = X[q * kk + i], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      double sacc[8];
+      sacc[0] = X[(size_t)q * kk + i];
+#pragma unroll
+      for (int r = 1; r < 8; ++r) sacc[r] = 0.0;
+      const double* Ri = S + (size_t)i * lds;
       int l = 0;
-      for (; l + 3 < i; l += 4) {
-        s0 -= M[i * kk + l] * C[l * kk + q]; s1 -= M[i * kk + l + 1] * C[(l + 1) * kk + q];
-        s2 -= M[i * kk + l + 2] * C[(l + 2) * kk + q]; s3 -= M[i * kk + l + 3] * C[(l + 3) * kk + q];
+      for (; l + 7 < i; l += 8) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) sacc[r] -= Ri[l + r] * Cg[(size_t)(l + r) * kk + q];
       }
-      for (; l < i; ++l) s0 -= M[i * kk + l] * C[l * kk + q];
-      C[i * kk + q] = ((s0 + s1) + (s2 + s3)) * rdiag[i];
+      for (; l < i; ++l) sacc[0] -= Ri[l] * Cg[(size_t)l * kk + q];
+      Cg[(size_t)i * kk + q] =
+          (((sacc[0] + sacc[1]) + (sacc[2] + sacc[3])) + ((sacc[4] + sacc[5]) + (sacc[6] + sacc[7]))) * rdiag[i];
     }
   }
   __syncthreads();
-  for (int idx = tid; idx < kk * kk; idx += nth) {   // symmetrise
-    int i = idx / kk, j = idx % kk;
-    if (i < j) { double v = 0.5 * (C[i * kk + j] + C[j * kk + i]); C[i * kk + j] = v; C[j * kk + i] = v; }
-  }
+  // 5. S = symmetrised C (lower triangle; R is no longer needed)
+  for (int i = wid; i < kk; i += nwarp)
+    for (int j = lane; j <= i; j += 32) S[i * lds + j] = 0.5 * (Cg[(size_t)i * kk + j] + Cg[(size_t)j * kk + i]);
   __syncthreads();
-  // 5. Householder tridiagonalisation C = Q T Q^T; pA, pD <- Q^T pA, Q^T pD.
-  double* u = X;            // reuse X rows as scratch vectors
-  double* p = X + kk;
+  // 6. Householder tridiagonalisation C = Q T Q^T on the lower triangle;
+  //    p_A, p_D <- Q^T p_A, Q^T p_D.
   for (int k = 0; k + 2 < kk; ++k) {
     const int len = kk - k - 1;
-    double part = 0.0;
-    for (int i = tid; i < len; i += nth) { double xv = C[(k + 1 + i) * kk + k]; part += xv * xv; }
-    const double nx2 = sel_block_sum(part, sh);
-    const double x0 = C[(k + 1) * kk + k];
-    if (nx2 - x0 * x0 <= 1e-300 * (1.0 + nx2)) continue;   // column already reduced
-    // u = (x - alpha e1) / ||x - alpha e1||, ||x - alpha e1||^2 = 2 nx (nx + |x0|)
-    __shared__ double s_alpha, s_inu;
+    double nx[1] = {0.0};
+    for (int i = tid; i < len; i += nth) {
+      const double xv = S[(k + 1 + i) * lds + k];
+      u[i] = xv;
+      nx[0] += xv * xv;
+    }
+    sel_sumN<1>(nx, len, sh);
+    const double nx2 = nx[0];
+    const double x0 = u[0];
+    if (nx2 - x0 * x0 <= 1e-300 * (1.0 + nx2)) continue;   // column already reduced (uniform)
     if (tid == 0) {
-      const double nx = sqrt(nx2);
-      s_alpha = x0 >= 0 ? -nx : nx;
-      s_inu = 1.0 / sqrt(2.0 * nx * (nx + fabs(x0)));
+      const double inx = rsqrt_d(nx2);
+      const double nrm = nx2 * inx;
+      const double alpha = x0 >= 0 ? -nrm : nrm;
+      s_bc[1] = alpha;
+      s_bc[2] = rsqrt_d(2.0 * nrm * (nrm + fabs(x0)));
     }
     __syncthreads();
-    const double alpha = s_alpha, inv_nu = s_inu;
-    for (int i = tid; i < len; i += nth) u[i] = (C[(k + 1 + i) * kk + k] - (i == 0 ? alpha : 0.0)) * inv_nu;
+    const double alpha = s_bc[1], inv_nu = s_bc[2];
+    for (int i = tid; i < len; i += nth) u[i] = (u[i] - (i == 0 ? alpha : 0.0)) * inv_nu;
     __syncthreads();
+    // p = C' u with C' the trailing block (lower storage: row part, then column part)
+    const double* Sb = S + (size_t)(k + 1) * lds + (k + 1);
     for (int i = tid; i < len; i += nth) {
-      const double* row = C + (size_t)(k + 1 + i) * kk + (k + 1);
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      double s4[4] = {0.0, 0.0, 0.0, 0.0};
+      const double* row = Sb + (size_t)i * lds;
       int j = 0;
-      for (; j + 3 < len; j += 4) { s0 += row[j] * u[j]; s1 += row[j + 1] * u[j + 1]; s2 += row[j + 2] * u[j + 2]; s3 += row[j + 3] * u[j + 3]; }
-      for (; j < len; ++j) s0 += row[j] * u[j];
-      p[i] = (s0 + s1) + (s2 + s3);
+      for (; j + 3 < i; j += 4) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) s4[r] += row[j + r] * u[j + r];
+      }
+      for (; j < i; ++j) s4[0] += row[j] * u[j];
+      j = i;
+      for (; j + 3 < len; j += 4) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) s4[r] += Sb[(size_t)(j + r) * lds + i] * u[j + r];
+      }
+      for (; j < len; ++j) s4[0] += Sb[(size_t)j * lds + i] * u[j];
+      p[i] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
     }
     __syncthreads();
-    double pk = 0.0, da = 0.0, dd = 0.0;
-    for (int i = tid; i < len; i += nth) { pk += u[i] * p[i]; da += u[i] * pA[k + 1 + i]; dd += u[i] * pD[k + 1 + i]; }
-    const double K = sel_block_sum(pk, sh);
-    da = sel_block_sum(da, sh);
-    dd = sel_block_sum(dd, sh);
-    for (int idx = tid; idx < len * len; idx += nth) {
-      const int i = idx / len, j = idx % len;
-      const double wi = 2.0 * p[i] - 2.0 * K * u[i], wj = 2.0 * p[j] - 2.0 * K * u[j];
-      C[(k + 1 + i) * kk + (k + 1 + j)] -= u[i] * wj + wi * u[j];
+    double kd[3] = {0.0, 0.0, 0.0};
+    for (int i = tid; i < len; i += nth) {
+      kd[0] += u[i] * p[i];
+      kd[1] += u[i] * pA[k + 1 + i];
+      kd[2] += u[i] * pD[k + 1 + i];
+    }
+    sel_sumN<3>(kd, len, sh);
+    const double K = kd[0], da = kd[1], dd = kd[2];
+    for (int i = tid; i < len; i += nth) p[i] = 2.0 * p[i] - 2.0 * K * u[i];   // w
+    __syncthreads();
+    for (int ii = wid; ii < len; ii += nwarp) {
+      const double ui = u[ii], wi = p[ii];
+      double* Si = S + (size_t)(k + 1 + ii) * lds + (k + 1);
+      for (int jj = lane; jj <= ii; jj += 32) Si[jj] -= ui * p[jj] + wi * u[jj];
     }
     for (int i = tid; i < len; i += nth) {
-      const double v = (i == 0) ? alpha : 0.0;
-      C[(k + 1 + i) * kk + k] = v;
-      C[k * kk + (k + 1 + i)] = v;
       pA[k + 1 + i] -= 2.0 * da * u[i];
       pD[k + 1 + i] -= 2.0 * dd * u[i];
     }
+    if (tid == 0) S[(size_t)(k + 1) * lds + k] = alpha;
     __syncthreads();
   }
   for (int i = tid; i < kk; i += nth) {
-    dg[i] = C[i * kk + i];
-    eo[i] = (i + 1 < kk) ? C[(i + 1) * kk + i] : 0.0;
+    dg[i] = S[(size_t)i * lds + i];
+    eo[i] = (i + 1 < kk) ? S[(size_t)(i + 1) * lds + i] : 0.0;
   }
   __syncthreads();
-  // 5b. w0 = T^{-1} p_A, f = p_A + p_D - w0, r0^2 = ||b||^2 - p_A . w0
-  double* fvec = scratch + (size_t)SEL_MAXPTS * 2 * kk;     // kk
-  __shared__ double s_r02;
+  // 6b. w0 = T^{-1} p_A, f = p_A + p_D - w0, r0^2 = ||b||^2 - p_A . w0.
+  //     One Thomas sweep: T can be numerically singular (exact mode on a tiny
+  //     level), where sequential elimination stays accurate and parallel
+  //     cyclic reduction does not.
   if (tid == 0) {
-    double* w0 = scratch;
-    sel_tri_solve(kk, dg, eo, pA, 0.0, scratch + kk, w0, 0.0);
+    sel_tri_solve(kk, dg, eo, pA, 0.0, p, u, 0.0);
     double pw = 0.0;
     for (int i = 0; i < kk; ++i) {
-      pw += pA[i] * w0[i];
-      fvec[i] = pA[i] + pD[i] - w0[i];
+      pw += pA[i] * u[i];
+      fvec[i] = pA[i] + pD[i] - u[i];
     }
-    const double r = a.bnorm2 - pw;
-    s_r02 = r > 0.0 ? r : 0.0;
+    s_bc[3] = pw;
   }
   __syncthreads();
-  const double r02 = s_r02;
-  // 6. exact mode: eigenvalues of T by bisection (Sturm counts), one per thread
+  const double r02 = (a.bnorm2 - s_bc[3]) > 0.0 ? (a.bnorm2 - s_bc[3]) : 0.0;
+  // 7. exact mode: eigenvalues of T by bisection (Sturm counts), one per thread
   if (a.exact) {
     double glo = 0.0, ghi = 0.0;
     for (int i = 0; i < kk; ++i) {   // Gershgorin interval
@@ -714,7 +1027,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_gcv_select(GcvSelectArgs a) {
     }
     __syncthreads();
   }
-  // 7. grid search (parallel over the grid points) with widening, then Brent
+  // 8. grid search (parallel over the grid points) with widening, then Brent
   const int npts = a.npts < SEL_MAXPTS ? a.npts : SEL_MAXPTS;
   double lo = a.lo, hi = a.hi;
   int ext = 0, jbest = 0;
@@ -723,7 +1036,12 @@ __global__ void __launch_bounds__(SEL_THREADS) k_gcv_select(GcvSelectArgs a) {
     step = (hi - lo) / (npts - 1);
     for (int j = tid; j < npts; j += nth) s_gam[j] = pow(10.0, (j == npts - 1) ? hi : lo + j * step);
     __syncthreads();
-    sel_traces(a, lam, npts, s_gam, s_tr, sh);
+    if (ext == 0 && a.trace_tab && !a.exact) {
+      for (int j = tid; j < npts; j += nth) s_tr[j] = a.trace_tab[j];
+      __syncthreads();
+    } else {
+      sel_traces(a, lam, npts, s_gam, s_tr, sh);
+    }
     for (int j = tid; j < npts; j += nth) {
       const double num = sel_numerator(kk, dg, eo, fvec, r02, s_gam[j], scratch + (size_t)j * 2 * kk,
                                        scratch + (size_t)j * 2 * kk + kk);
@@ -741,25 +1059,18 @@ __global__ void __launch_bounds__(SEL_THREADS) k_gcv_select(GcvSelectArgs a) {
     break;
   }
   auto tgrid = [&](int j) { return (j == npts - 1) ? hi : lo + j * step; };
+  // S is free once T is extracted: scratch of the trial-gamma solves
   auto feval = [&](double t) -> double {
+    const double gam = pow(10.0, t);
+    const double num = sel_eval(a, kk, dg, eo, fvec, r02, lam, gam, u, S, sh, &s_bc[2]);
+    const double den = a.n - s_bc[2];
     __syncthreads();
-    if (tid == 0) s_gam[0] = pow(10.0, t);
-    __syncthreads();
-    sel_traces(a, lam, 1, s_gam, s_tr, sh);
-    if (tid == 0) {
-      const double num = sel_numerator(kk, dg, eo, fvec, r02, s_gam[0], scratch, scratch + kk);
-      const double den = a.n - s_tr[0];
-      s_f[0] = num / (den * den);
-    }
-    __syncthreads();
-    const double f = s_f[0];
-    __syncthreads();
-    return f;
+    return num / (den * den);
   };
   double A = tgrid(jbest > 0 ? jbest - 1 : 0);
   double B = tgrid(jbest < npts - 1 ? jbest + 1 : npts - 1);
   // Brent (golden section + parabolic interpolation); every thread runs the
-  // same control flow on the same broadcast values.
+  // same control flow on the same values.
   const double cgold = 0.5 * (3.0 - sqrt(5.0));
   const double sqeps = sqrt(2.220446049250313e-16);
   double x = A + cgold * (B - A), w = x, v = x;

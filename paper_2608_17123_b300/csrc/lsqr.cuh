@@ -348,6 +348,97 @@ __device__ __forceinline__ int lsqr_finish_B(LsqrState S, LsqrState* st, LsqrCoe
   return S.done;
 }
 
+// Per-tile partial of the three sums into part[tile*3 .. tile*3+2] (24 bytes).
+// Float working precision: TwoSum butterflies within the warps and across
+// them, stored as (hi, lo) float pairs -- no FP64 instruction, whose issue
+// costs ~64 cycles per warp instruction on this part. Double working
+// precision: FP64 block sum, stored as doubles.
+__device__ __forceinline__ void tile_partial(const float (&red)[3], double* part_tile, double* scratch) {
+  const int tid = threadIdx.x + 32 * threadIdx.y, lane = tid & 31, wid = tid >> 5;
+  float2* sw = reinterpret_cast<float2*>(scratch);          // [3][8]
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float2 r = warp_df(red[k], 0.f);
+    if (lane == 0) sw[k * 8 + wid] = r;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    float2* out = reinterpret_cast<float2*>(part_tile);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float h = lane < TY ? sw[k * 8 + lane].x : 0.f, l = lane < TY ? sw[k * 8 + lane].y : 0.f;
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+        df_add(h, l, h2, l2);
+      }
+      if (lane == 0) out[k] = make_float2(h, l);
+    }
+  }
+}
+__device__ __forceinline__ void tile_partial(const double (&red)[3], double* part_tile, double* scratch) {
+  double tot[3];
+  block_sum_to0<3, double>(red, tot, scratch);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) part_tile[k] = tot[k];
+  }
+}
+
+// Sum of a problem's tile partials by one warp, in tile order; result in lane 0.
+template <typename Acc>
+__device__ __forceinline__ void problem_partials(const double* part, int ntiles, double (&tot)[3]);
+template <>
+__device__ __forceinline__ void problem_partials<float>(const double* part, int ntiles, double (&tot)[3]) {
+  constexpr int PB = 8;
+  const int lane = threadIdx.x;
+  const float2* pp = reinterpret_cast<const float2*>(part);
+  float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+  for (int t0 = lane; t0 < ntiles; t0 += 32 * PB) {
+    float2 q[PB][3];
+#pragma unroll
+    for (int b = 0; b < PB; ++b) {
+      const int t = t0 + 32 * b;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) q[b][k] = t < ntiles ? __ldcg(pp + (size_t)t * 3 + k) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int b = 0; b < PB; ++b)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) df_add(h[k], l[k], q[b][k].x, q[b][k].y);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, h[k], o), l2 = __shfl_xor_sync(0xffffffffu, l[k], o);
+      df_add(h[k], l[k], h2, l2);
+    }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) tot[k] = (double)h[k] + (double)l[k];
+}
+template <>
+__device__ __forceinline__ void problem_partials<double>(const double* part, int ntiles, double (&tot)[3]) {
+  constexpr int PB = 8;
+  const int lane = threadIdx.x;
+  tot[0] = tot[1] = tot[2] = 0.0;
+  for (int t0 = lane; t0 < ntiles; t0 += 32 * PB) {
+    double q[PB][3];
+#pragma unroll
+    for (int b = 0; b < PB; ++b) {
+      const int t = t0 + 32 * b;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) q[b][k] = t < ntiles ? __ldcg(part + (size_t)t * 3 + k) : 0.0;
+    }
+#pragma unroll
+    for (int b = 0; b < PB; ++b)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) tot[k] += q[b][k];
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) tot[k] = warp_sum(tot[k]);
+}
+
 // End of a phase: every block has written its tiles' partials. The last block
 // to arrive at the grid barrier reduces every problem's partials (warp w takes
 // problems w, w + 8, ...; fixed order over tiles), runs the scalar updates,
@@ -379,28 +470,11 @@ __device__ int lsqr_phase_end(const LsqrProb<T, Acc>* probs, const LsqrCtl& ctl,
     const int warp = tid >> 5, lane = tid & 31;
     for (int p = warp; p < ctl.nprob; p += (32 * TY) / 32) {
       const LsqrProb<T, Acc>& P = probs[p];
-      // state and tile partials requested together; partials in batches of
-      // PB per lane (one memory round trip per batch), summed in tile order
-      constexpr int PB = 8;
+      // state and tile partials requested together, partials summed in tile order
       LsqrState S;
       if (lane == 0) S = load_state(&ctl.st[p]);
-      const double* part = ctl.part + (size_t)P.tile_begin * 3;
-      double tot[3] = {0.0, 0.0, 0.0};
-      for (int t0 = lane; t0 < P.ntiles; t0 += 32 * PB) {
-        double q[PB][3];
-#pragma unroll
-        for (int b = 0; b < PB; ++b) {
-          const int t = t0 + 32 * b;
-#pragma unroll
-          for (int k = 0; k < 3; ++k) q[b][k] = t < P.ntiles ? __ldcg(part + (size_t)t * 3 + k) : 0.0;
-        }
-#pragma unroll
-        for (int b = 0; b < PB; ++b)
-#pragma unroll
-          for (int k = 0; k < 3; ++k) tot[k] += q[b][k];
-      }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) tot[k] = warp_sum(tot[k]);
+      double tot[3];
+      problem_partials<Acc>(ctl.part + (size_t)P.tile_begin * 3, P.ntiles, tot);
       if (lane == 0 && !S.done) {
         const int done = isF ? lsqr_finish_F<Acc>(ctl, S, &ctl.st[p], coef + p, it == 0, it, tot)
                              : lsqr_finish_B<Acc>(S, &ctl.st[p], coef + p, it == 0, tot);
@@ -434,21 +508,40 @@ __device__ int lsqr_phase_end(const LsqrProb<T, Acc>* probs, const LsqrCtl& ctl,
   return s_dec;
 }
 
+constexpr int LSQR_TCACHE = 4;   // tile descriptors a block keeps in shared memory
+
 template <typename T, typename Acc>
 __global__ void __launch_bounds__(256, 2) k_lsqr(const LsqrProb<T, Acc>* __restrict__ probs, LsqrCtl ctl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Acc* sm = reinterpret_cast<Acc*>(smem_raw);
   __shared__ double scratch[3 * 32];
+  __shared__ __align__(16) LsqrProb<T, Acc> s_prob[LSQR_TCACHE];
+  __shared__ int s_pid[LSQR_TCACHE];
   LsqrCoef<Acc>* coef = reinterpret_cast<LsqrCoef<Acc>*>(ctl.coef);
   const unsigned G = gridDim.x;
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  // the descriptors of this block's first tiles stay in shared memory for the
+  // whole launch (the loads after a grid barrier then start from registers)
+  for (int k = 0; k < LSQR_TCACHE; ++k) {
+    const int tile = blockIdx.x + k * (int)G;
+    if (tile >= ctl.ntiles) break;
+    const int p = __ldg(ctl.tile_prob + tile);
+    const int* src = reinterpret_cast<const int*>(probs + p);
+    int* dst = reinterpret_cast<int*>(&s_prob[k]);
+    for (int w = tid; w < (int)(sizeof(LsqrProb<T, Acc>) / sizeof(int)); w += 32 * TY) dst[w] = src[w];
+    if (tid == 0) s_pid[k] = p;
+  }
+  __syncthreads();
   // phase 0: F(init), B(init); then F_i, B_i for i = 1, 2, ... until every
   // problem has stopped (decided by the last block at each barrier)
   for (int it = 0;; ++it) {
     for (int half = 0; half < 2; ++half) {
       const bool isF = (half == 0);
-      for (int tile = blockIdx.x; tile < ctl.ntiles; tile += G) {
-        const int p = __ldg(ctl.tile_prob + tile);
-        const LsqrProb<T, Acc>& P = probs[p];
+      int k = 0;
+      for (int tile = blockIdx.x; tile < ctl.ntiles; tile += G, ++k) {
+        const bool cached = k < LSQR_TCACHE;
+        const int p = cached ? s_pid[k] : __ldg(ctl.tile_prob + tile);
+        const LsqrProb<T, Acc>& P = cached ? s_prob[k] : probs[p];
         const int tl = tile - P.tile_begin;
         const int r0 = (tl % P.nt) * TM, c0 = (tl / P.nt) * TN;
         Acc red[3];
@@ -456,12 +549,7 @@ __global__ void __launch_bounds__(256, 2) k_lsqr(const LsqrProb<T, Acc>* __restr
         const bool did = isF ? lsqr_pass_F<T, Acc>(P, ctl, p, it == 0, it == 1, r0, c0, sm, red)
                              : lsqr_pass_B<T, Acc>(P, ctl, p, it == 0, r0, c0, sm, red);
         if (!did) continue;   // uniform over the block
-        double tot[3];
-        block_sum_to0<3, Acc>(red, tot, scratch);
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-#pragma unroll
-          for (int k = 0; k < 3; ++k) ctl.part[(size_t)tile * 3 + k] = tot[k];
-        }
+        tile_partial(red, ctl.part + (size_t)tile * 3, scratch);
       }
       const int dec = lsqr_phase_end<T, Acc>(probs, ctl, coef, isF, it);
       if (dec != 0) return;

@@ -34,13 +34,22 @@ def test_gcv_matches_oracle(prec, kind, m):
     a0 = a1 = None
     if kind == "irls":
         a0 = S.irls_weights(qx, qy, 0.03)
-        sub = S.Subproblem(A, b, weights=a0)
     elif kind == "mm":
         a0 = S.mm_surrogate(qx, qy, 0.03)
-        sub = S.Subproblem(A, b, c=a0)
     elif kind == "sb":
         a0 = (S.shrink(qx, 0.005), S.shrink(qy, 0.005))
         a1 = (0.5 * (qx - a0[0]), 0.5 * (qy - a0[1]))
+    # the oracle sees exactly the inputs the GPU call receives (FP32 buffers
+    # hold b and the planes rounded to float32)
+    rnd = (lambda v: v.astype(np.float32).astype(np.float64)) if prec == "fp32" else (lambda v: v)
+    b = rnd(b)
+    a0 = None if a0 is None else tuple(rnd(v) for v in a0)
+    a1 = None if a1 is None else tuple(rnd(v) for v in a1)
+    if kind == "irls":
+        sub = S.Subproblem(A, b, weights=a0)
+    elif kind == "mm":
+        sub = S.Subproblem(A, b, c=a0)
+    elif kind == "sb":
         sub = S.Subproblem(A, b, c=(a0[0] - a1[0], a0[1] - a1[1]))
     else:
         sub = S.Subproblem(A, b)
@@ -67,6 +76,9 @@ def test_gcv_exact_mode_tiny_level(prec, kind):
     if kind == "mm":
         qx, qy = O.L_apply(0.8 * x_true)
         a0 = S.mm_surrogate(qx, qy, 0.03)
+    if prec == "fp32":          # the oracle sees the float32-rounded inputs the GPU receives
+        b = b.astype(np.float32).astype(np.float64)
+        a0 = None if a0 is None else tuple(v.astype(np.float32).astype(np.float64) for v in a0)
     sub = S.Subproblem(A, b, c=a0)
     g_ref = sub.gcv(S.opts_with())
     g_sp = noisy(lambda: sub.gcv(S.opts_with()), prec)
