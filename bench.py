@@ -131,6 +131,27 @@ def make_inputs(api, torch, s, psf_dev):
     return b, x_true
 
 
+# ------------------------------------------------------------------ sharding
+def shard_steps(rank, warmup, steps):
+    """Step indices of one rank: every rank solves its own images (weak
+    scaling, no data-path collective), rank r taking a disjoint block."""
+    total = warmup + steps
+    return [rank * total + i for i in range(total)]
+
+
+def max_over_ranks(t_ms, world):
+    """Largest per-rank time (the job's wall time); a collective only when
+    there is more than one rank (NCCL on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return float(t_ms)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(t_ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world):
     import torch
@@ -144,7 +165,7 @@ def run_ours(args, rank, world):
     psf_dev = torch.from_numpy(I.to_colmajor(psf).ravel()).cuda()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     total = args.warmup + args.steps
-    steps = [rank * total + i for i in range(total)]
+    steps = shard_steps(rank, args.warmup, args.steps)
     # inputs resident in HBM before timing
     dev_inputs = []
     host_inputs = []
@@ -185,13 +206,10 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     clk = clocks.stop()
     stats = ctx.stats()
-    t_total_ms = sum(times)
+    t_total_ms = max_over_ranks(sum(times), world)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([t_total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-        t_total_ms = float(t.item())
     pixels = M * M * args.steps * world
     value = pixels / (t_total_ms / 1e3) / 1e6
 
@@ -250,6 +268,8 @@ def run_ours(args, rank, world):
         "clocks": clk,
         "counts": {"lsqr_launches": int(stats["lsqr_launches"]), "gcv_calls": int(stats["gcv_calls"]),
                    "outer_iterations": int(stats["outer_iterations"])},
+        "step_split": {"lsqr_ms_per_step": round(stats["lsqr_ms"] / args.steps, 2),
+                       "gcv_ms_per_step": round(stats.get("gcv_ms", 0.0) / args.steps, 2)},
     }
     line.update(forms)
     return line, per_level_counts, times
@@ -259,7 +279,9 @@ def run_forms(api, ctx, torch, bs, step_ids, psf):
     """Images/s of the plain one-at-a-time host call, the batched call
     (deblur_solve_batch) and the serving loop (db_server_*, all requests
     queued at once) on the same images, with the largest relative difference
-    of the batched and served reconstructions from the plain ones."""
+    of the batched and served reconstructions from the plain ones; then a
+    Poisson request stream at 80 % of the batched throughput (each image
+    twice) with its p50/p99 latency."""
     from paper_2608_17123_b300 import inputs as I
     imgs = [I.from_colmajor(b, M) for b in bs]
     specs = [step_spec(s) for s in step_ids]
@@ -287,8 +309,28 @@ def run_forms(api, ctx, torch, bs, step_ids, psf):
     def rel(a, b):
         return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
+    # Poisson arrivals at 80 % of the batched throughput, each image twice:
+    # latency from submit to completion as the server reports it
+    rng = np.random.default_rng(2026)
+    rate = 0.8 * len(imgs) / t_batch
+    order = [i % len(imgs) for i in range(2 * len(imgs))]
+    gaps = rng.exponential(1.0 / rate, size=len(order))
+    srv = api.Server(max_resident=len(imgs), max_m=M)
+    t0 = time.perf_counter()
+    tks, t_next = [], 0.0
+    for k, i in enumerate(order):
+        t_next += gaps[k]
+        while time.perf_counter() - t0 < t_next:
+            time.sleep(0.0005)
+        sp = specs[i]
+        tks.append(srv.submit(imgs[i], psf, sp[0], sp[1], LEVELS, sp[2]))
+    lat_p = [srv.poll(tk)[1] for tk in tks]
+    t_poisson = time.perf_counter() - t0
+    srv.close()
     n = len(imgs)
     lat_sorted = sorted(lat)
+    poisson = {"rate_per_s": round(rate, 3), "requests": len(order), "images_per_s": round(len(order) / t_poisson, 4),
+               "p50_ms": round(float(np.percentile(lat_p, 50)), 2), "p99_ms": round(float(np.percentile(lat_p, 99)), 2)}
     return {
         "plain_images_per_s": round(n / t_plain, 4),
         "batched": {"images_per_s": round(n / t_batch, 4), "images": n, "call": "deblur_solve_batch",
@@ -296,7 +338,8 @@ def run_forms(api, ctx, torch, bs, step_ids, psf):
         "serving": {"images_per_s": round(n / t_srv, 4), "requests": n, "arrival": "all queued at t=0",
                     "p50_ms": round(float(np.percentile(lat_sorted, 50)), 2),
                     "p99_ms": round(float(np.percentile(lat_sorted, 99)), 2),
-                    "max_rel_diff_vs_plain": max(rel(q["x"], p["x"]) for q, p in zip(served, plain))},
+                    "max_rel_diff_vs_plain": max(rel(q["x"], p["x"]) for q, p in zip(served, plain)),
+                    "poisson": poisson},
     }
 
 

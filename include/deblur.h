@@ -187,7 +187,8 @@ db_status db_server_destroy(db_server* srv);
  * launch count, device time (CUDA events recorded on the launching stream
  * around each launch when db_set_profiling(ctx, 1) is on) and the LSQR
  * iterations x pixels it processed, split by solver family (IRLS reads the
- * weight planes in both passes). */
+ * weight planes in both passes); with profiling on, also the wall time spent
+ * in GCV selections (each ends with a synchronisation of its stream). */
 typedef struct {
   uint64_t kernel_launches;
   uint64_t lsqr_launches;
@@ -196,9 +197,18 @@ typedef struct {
   double   lsqr_pixel_iters_other;
   uint64_t gcv_calls;
   uint64_t outer_iterations;
+  double   gcv_ms;
 } db_stats;
 
 db_status db_set_profiling(db_context* ctx, int on);
+/* Launch-shape autotuner (on by default; no counterpart in the paper): the
+ * first LSQR launch of a size class (storage type, tile-count bucket, PSF
+ * rank one or not, band width) times each shape -- blocks per SM capped at
+ * 1 or 2, band-row cache on or off -- as a complete solve on the live inputs
+ * and keeps the fastest for the context's life. All shapes compute the same
+ * result bit for bit, so tuning changes timing only. on = 0 uses the first
+ * shape (2 blocks per SM, cache on) without timing. */
+db_status db_set_autotune(db_context* ctx, int on);
 db_status db_get_stats(db_context* ctx, db_stats* out);
 db_status db_reset_stats(db_context* ctx);
 

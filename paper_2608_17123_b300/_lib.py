@@ -38,7 +38,7 @@ class DbGcvOpts(C.Structure):
 class DbStats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("lsqr_launches", C.c_uint64), ("lsqr_ms", C.c_double),
                 ("lsqr_pixel_iters_irls", C.c_double), ("lsqr_pixel_iters_other", C.c_double),
-                ("gcv_calls", C.c_uint64), ("outer_iterations", C.c_uint64)]
+                ("gcv_calls", C.c_uint64), ("outer_iterations", C.c_uint64), ("gcv_ms", C.c_double)]
 
 
 class DbRequest(C.Structure):
@@ -76,6 +76,7 @@ _SIGS = {
     "db_server_poll": (C.c_int, [_VP, C.c_uint64, C.c_int, C.POINTER(C.c_double)]),
     "db_server_destroy": (C.c_int, [_VP]),
     "db_set_profiling": (C.c_int, [_VP, C.c_int]),
+    "db_set_autotune": (C.c_int, [_VP, C.c_int]),
     "db_get_stats": (C.c_int, [_VP, C.POINTER(DbStats)]),
     "db_reset_stats": (C.c_int, [_VP]),
     "db_apply_blur": (C.c_int, [_VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_int, _VP]),

@@ -41,6 +41,9 @@ class Context:
     def set_profiling(self, on=True):
         L.check(L.lib().db_set_profiling(self.handle, int(on)), self.handle)
 
+    def set_autotune(self, on=True):
+        L.check(L.lib().db_set_autotune(self.handle, int(on)), self.handle)
+
     def stats(self):
         st = L.DbStats()
         L.check(L.lib().db_get_stats(self.handle, C.byref(st)), self.handle)

@@ -92,6 +92,24 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float xh, float xl)
   hi = s;
 }
 
+// (hi, lo) += p[0], p[1], ..., p[n-1] in that order, the loads issued in
+// batches of 8 (L1 bypassed: the partials were written by other blocks), so
+// the chain waits for one memory round trip per batch, not per element.
+__device__ __forceinline__ void df_sum_loads(const float2* p, int n, float& hi, float& lo) {
+  int c = 0;
+  for (; c + 8 <= n; c += 8) {
+    float2 q[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[k] = __ldcg(p + c + k);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) df_add(hi, lo, q[k].x, q[k].y);
+  }
+  for (; c < n; ++c) {
+    const float2 v = __ldcg(p + c);
+    df_add(hi, lo, v.x, v.y);
+  }
+}
+
 // Kahan-compensated warp dot over strided elements, returned as (hi, lo).
 __device__ __forceinline__ float2 warp_df(float acc, float comp) {
   // combine acc (with Kahan residue -comp) across the warp

@@ -41,7 +41,8 @@ struct DbError {
     cudaError_t e_ = (call);                                                      \
     if (e_ != cudaSuccess) {                                                      \
       cudaGetLastError();                                                         \
-      throw DbError{DB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+      throw DbError{DB_ECUDA, std::string(#call) + " (deblur.cu:" + std::to_string(__LINE__) + "): " + \
+                                  cudaGetErrorString(e_)};                                        \
     }                                                                             \
   } while (0)
 
@@ -89,7 +90,20 @@ struct db_context {
   Arena arena;
   std::string err;
   db_stats stats{};
-  std::atomic<uint64_t> n_launches{0}, n_gcv{0};
+  std::atomic<uint64_t> n_launches{0}, n_gcv{0}, gcv_ns{0};
+  // launch-shape autotuner: size class -> chosen shape (see lsqr_launch)
+  int autotune = 1;
+  std::mutex tune_mu;
+  std::map<uint64_t, int> tune_lsqr;
+  int tuned(uint64_t key) {
+    std::lock_guard<std::mutex> lk(tune_mu);
+    auto it = tune_lsqr.find(key);
+    return it == tune_lsqr.end() ? -1 : it->second;
+  }
+  void set_tuned(uint64_t key, int v) {
+    std::lock_guard<std::mutex> lk(tune_mu);
+    tune_lsqr[key] = v;
+  }
   int profiling = 0;
   // factorisation of the last PSF (separable terms), reused while the PSF is unchanged
   std::vector<double> psf_key;
@@ -133,7 +147,121 @@ static int grid_for(size_t n, int nsm, int per = 256) {
   return (int)g;
 }
 
+// Band-row cache of the LSQR kernel: on when every problem of the launch has
+// a one-term (separable) blur and the cache (LSQR_TCACHE tiles x forward and
+// transposed row and column bands) fits in 48 KB; sets the LsqrCtl fields and
+// returns the extra dynamic shared memory in bytes.
+template <typename Acc>
+static int lsqr_band_cache(LsqrCtl& c, int tile_bytes, const BandOp<Acc>* ops, int nops) {
+  c.band_cache = 0;
+  c.band_pw = 0;
+  c.cache_off = (tile_bytes + (int)sizeof(Acc) - 1) / (int)sizeof(Acc);
+  int pw = 0;
+  for (int i = 0; i < nops; ++i) {
+    if (ops[i].nterms != 1) return 0;
+    pw = std::max(pw, band_pitch(ops[i].w));
+  }
+  const int bytes = LSQR_TCACHE * 4 * TM * pw * (int)sizeof(Acc);
+  if (nops < 1 || bytes > 48 * 1024) return 0;
+  c.band_cache = 1;
+  c.band_pw = pw;
+  return c.cache_off * (int)sizeof(Acc) - tile_bytes + bytes;
+}
+
+// Launch shapes of the LSQR kernel the autotuner chooses between: the cap on
+// resident blocks per SM (which sets how many tiles each block takes) and
+// the band-row cache. Every shape computes the same result -- a tile's
+// partial sums depend only on the tile and are added in tile order -- so the
+// choice changes the time only.
+struct LsqrShape {
+  int per_sm_cap;
+  int band_cache;
+};
+static const LsqrShape kLsqrShapes[4] = {{2, 1}, {2, 0}, {1, 1}, {1, 0}};
+
+// Size class of an LSQR launch for the autotuner: storage size, tile count
+// (power-of-two bucket), whether every blur has one term, widest band.
+template <typename Acc>
+static uint64_t lsqr_size_class(int elem_bytes, int ntiles, const BandOp<Acc>* ops, int nops) {
+  int one = 1, w = 0;
+  for (int i = 0; i < nops; ++i) {
+    one &= ops[i].nterms == 1;
+    w = std::max(w, ops[i].w);
+  }
+  int b = 0;
+  while ((1 << b) < ntiles) ++b;
+  return ((uint64_t)elem_bytes << 40) | ((uint64_t)b << 32) | ((uint64_t)one << 24) | (uint64_t)w;
+}
+
+template <typename T, typename Acc>
+static void lsqr_launch(db_context* ctx, cudaStream_t st, const LsqrProb<T, Acc>* d_probs, LsqrCtl c, int ntiles,
+                        int tile_bytes, const BandOp<Acc>* ops, int nops, LsqrShape shape) {
+  int sm = tile_bytes;
+  if (shape.band_cache) {
+    sm += lsqr_band_cache<Acc>(c, tile_bytes, ops, nops);
+  } else {
+    c.band_cache = 0;
+    c.band_pw = 0;
+    c.cache_off = 0;
+  }
+  auto kfn = k_lsqr<T, Acc>;
+  // the opt-in limit is set to the exact size every time: static plus dynamic
+  // shared memory may pass the 48 KB default even when the dynamic part alone
+  // does not
+  CK(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, sm));
+  if (per_sm < 1) throw DbError{DB_EINVAL, "LSQR kernel does not fit on an SM (" + std::to_string(sm) +
+                                           " bytes of dynamic shared memory)"};
+  per_sm = std::min(per_sm, shape.per_sm_cap);
+  const int grid = std::max(1, std::min(ntiles, per_sm * ctx->nsm));
+  void* args[] = {(void*)&d_probs, (void*)&c};
+  count_launch();
+  CK(cudaLaunchCooperativeKernel((const void*)kfn, dim3(grid), dim3(32, TY), args, sm, st));
+}
+
+// Runs one LSQR launch; on the first launch of a size class (autotune on)
+// runs every shape on the same inputs, each a complete solve from the reset
+// state, and keeps the fastest. Returns the device time of the launch whose
+// results stay in the buffers (the last one run), in ms (profiling or tuning).
+template <typename T, typename Acc, typename Reset>
+static float lsqr_run(db_context* ctx, cudaStream_t st, const LsqrProb<T, Acc>* d_probs, const LsqrCtl& c,
+                      int ntiles, int tile_bytes, const BandOp<Acc>* ops, int nops, GridBarrier* d_gb, Reset reset) {
+  const uint64_t key = lsqr_size_class<Acc>((int)sizeof(T), ntiles, ops, nops);
+  int choice = ctx->tuned(key);
+  const bool tune = choice < 0 && ctx->autotune;
+  if (choice < 0) choice = 0;
+  const int first = tune ? 0 : choice, last = tune ? 3 : choice;
+  float best = 1e30f, ms = 0.f;
+  if ((tune || ctx->profiling) && !ctx->ev0) {
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    if (!ctx->ev0) {
+      CK(cudaEventCreate(&ctx->ev1));
+      CK(cudaEventCreate(&ctx->ev0));
+    }
+  }
+  for (int s = first; s <= last; ++s) {
+    reset();
+    const bool timed = tune || ctx->profiling;
+    if (timed) CK(cudaEventRecord(ctx->ev0, st));
+    lsqr_launch<T, Acc>(ctx, st, d_probs, c, ntiles, tile_bytes, ops, nops, kLsqrShapes[s]);
+    if (timed) {
+      CK(cudaEventRecord(ctx->ev1, st));
+      CK(cudaEventSynchronize(ctx->ev1));
+      CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+      GridBarrier gbh;
+      CK(cudaMemcpyAsync(&gbh, d_gb, sizeof(gbh), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (gbh.error) throw DbError{DB_ETIMEOUT, "LSQR grid barrier timed out"};
+      if (ms < best) { best = ms; choice = s; }
+    }
+  }
+  if (tune) ctx->set_tuned(key, choice);
+  return ms;
+}
+
 // ============================================================================
+// level hierarchy// ============================================================================
 // level hierarchy
 // ============================================================================
 template <typename T>
@@ -229,7 +357,7 @@ struct GcvBufs {
     size_t tot = n0 * sizeof(Acc) * (kmax + 9);
     tot += (size_t)kmax * kmax * sizeof(double) * 8 + (size_t)kmax * 4096 * sizeof(double);
     tot += (size_t)exact_max * exact_max * sizeof(double) + (size_t)kmax * 160 * sizeof(double);
-    tot += (size_t)(2 * kmax + 4) * std::max<size_t>((n0 + 2047) / 2048, (size_t)4 * nsm) * 8;
+    tot += (size_t)std::max(2 * kmax + 4, (kmax + 1) * GDB_NB) * std::max<size_t>((n0 + 2047) / 2048, (size_t)4 * nsm) * 8;
     return tot + 64 * 4096 + 1024;
   }
 
@@ -257,7 +385,7 @@ struct GcvBufs {
     kc_epoch = 0;
     kc_cols = 0;
     const size_t nch = std::max<size_t>((n0 + VCH_CHUNK - 1) / VCH_CHUNK, (size_t)4 * nsm);
-    gpart2_cap = (size_t)(2 * kmax + 4) * nch;
+    gpart2_cap = (size_t)std::max(2 * kmax + 4, (kmax + 1) * GDB_NB) * nch;
     gpart2 = A.take<float2>(gpart2_cap);
     gmdot_part = A.take<double>((size_t)kmax * 256);
   }
@@ -324,7 +452,7 @@ struct Engine {
       tot += (size_t)mi * (S + 64) * (sizeof(double) * 2 + sizeof(Acc) * 4) * S + 4096;
       tot += (size_t)4 * S * m * 16;
     }
-    return tot + ((size_t)m * m / 1024 + 64) * 3 * sizeof(double) + 8 * 4096 + ((size_t)2 * S * S + S) * 8;
+    return tot + ((size_t)m * m / 1024 + 64) * 6 * sizeof(double) + 8 * 4096 + ((size_t)2 * S * S + S) * 8;
   }
 
   static size_t footprint(int m, int levels, int S, const db_gcv_opts& g) {
@@ -440,7 +568,7 @@ struct Engine {
     const size_t n0 = (size_t)m * m;
     size_t ntiles = 0;
     for (auto& L : H.lv) ntiles = std::max(ntiles, (size_t)L.ntiles_side() * L.ntiles_side());
-    part_cap = std::max<size_t>(ntiles * 3 + 64, 8192);
+    part_cap = std::max<size_t>(ntiles * 6 + 64, 8192);   // LSQR tile partials, two phase buffers
     d_part = A.take<double>(part_cap);
     d_cnt = A.take<unsigned>(64);
     d_box = A.take<double>(64);
@@ -517,28 +645,18 @@ struct Engine {
     CK(cudaMemcpyAsync(d_prob, &P, sizeof(P), cudaMemcpyHostToDevice, st));
     std::vector<int> tp(P.ntiles, 0);
     CK(cudaMemcpyAsync(d_tile_prob, tp.data(), sizeof(int) * tp.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(d_st, 0, sizeof(LsqrState), st));
-    CK(cudaMemsetAsync(d_coef, 0, sizeof(LsqrCoef<Acc>), st));
-    CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned), st));
-    CK(cudaMemsetAsync(d_gb, 0, sizeof(GridBarrier), st));
     LsqrCtl c;
     c.atol = o.lsqr_atol; c.btol = o.lsqr_btol; c.conlim = o.lsqr_conlim; c.maxit = o.lsqr_maxit;
     c.nprob = 1; c.ntiles = P.ntiles;
     c.tile_prob = d_tile_prob; c.part = d_part; c.cnt = d_cnt; c.st = d_st; c.gb = d_gb; c.coef = d_coef;
     c.limit_ns = 2000000000ull;
-    const int sm = smem_bytes(P.op);
-    auto kfn = k_lsqr<T, Acc>;
-    if (sm > 48 * 1024) CK(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    int per_sm = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, sm));
-    REQUIRE(per_sm >= 1, "LSQR kernel does not fit on an SM");
-    const int grid = std::max(1, std::min(P.ntiles, per_sm * ctx->nsm));
-    const LsqrProb<T, Acc>* pp = d_prob;
-    void* args[] = {(void*)&pp, (void*)&c};
-    if (ctx->profiling) CK(cudaEventRecord(ctx->ev0, st));
-    count_launch();
-    CK(cudaLaunchCooperativeKernel((const void*)kfn, dim3(grid), dim3(32, TY), args, sm, st));
-    if (ctx->profiling) CK(cudaEventRecord(ctx->ev1, st));
+    auto reset = [&]() {
+      CK(cudaMemsetAsync(d_st, 0, sizeof(LsqrState), st));
+      CK(cudaMemsetAsync(d_coef, 0, sizeof(LsqrCoef<Acc>), st));
+      CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned), st));
+      CK(cudaMemsetAsync(d_gb, 0, sizeof(GridBarrier), st));
+    };
+    const float lsqr_ms = lsqr_run<T, Acc>(ctx, st, d_prob, c, P.ntiles, smem_bytes(P.op), &P.op, 1, d_gb, reset);
     LsqrState S;
     GridBarrier gbh;
     CK(cudaMemcpyAsync(&S, d_st, sizeof(S), cudaMemcpyDeviceToHost, st));
@@ -550,11 +668,7 @@ struct Engine {
     const double pix = (double)(S.its + 1) * (double)L.n;
     if (solver == DB_IRLS) ctx->stats.lsqr_pixel_iters_irls += pix;
     else ctx->stats.lsqr_pixel_iters_other += pix;
-    if (ctx->profiling) {
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
-      ctx->stats.lsqr_ms += ms;
-    }
+    if (ctx->profiling) ctx->stats.lsqr_ms += lsqr_ms;
     return S.its;
   }
 
@@ -612,10 +726,15 @@ struct Engine {
       as[i].trace_tab = tab;
       kmax = std::max(kmax, as[i].kk);
     }
-    const size_t sm = sel_smem_bytes(kmax);
-    CK(cudaFuncSetAttribute(k_gcv_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    { count_launch(); k_gcv_select<<<na, SEL_THREADS, sm, st>>>(as[0], as[na > 1 ? 1 : 0], as[na > 2 ? 2 : 0]); }
-    CK(cudaGetLastError());
+    bool cluster = true;
+    for (int i = 0; i < na; ++i) cluster = cluster && !as[i].exact && as[i].kk <= SCL_MAXK;
+    if (cluster) cluster = launch_select_cluster(as, na, kmax);
+    if (!cluster) {
+      const size_t sm = sel_smem_bytes(kmax);
+      CK(cudaFuncSetAttribute(k_gcv_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      { count_launch(); k_gcv_select<<<na, SEL_THREADS, sm, st>>>(as[0], as[na > 1 ? 1 : 0], as[na > 2 ? 2 : 0]); }
+      CK(cudaGetLastError());
+    }
     std::vector<double> g(na);
     for (int i = 0; i < na; ++i) CK(cudaMemcpyAsync(&g[i], as[i].out, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -623,8 +742,47 @@ struct Engine {
   }
   double select(GcvSelectArgs a) { return select_multi(&a, 1)[0]; }
 
+  // One cluster of SCL_NC CTAs per selection (k_gcv_select_cl). Returns false
+  // (nothing launched) when the device cannot hold such a cluster.
+  bool launch_select_cluster(GcvSelectArgs* as, int na, int kmax) {
+    const size_t sm = scl_layout(kmax).total * sizeof(double);
+    if (cudaFuncSetAttribute(k_gcv_select_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(SCL_NC * na);
+    cfg.blockDim = dim3(SCL_THREADS);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = SCL_NC;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_gcv_select_cl, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      return false;
+    }
+    count_launch();
+    CK(cudaLaunchKernelEx(&cfg, k_gcv_select_cl, as[0], as[na > 1 ? 1 : 0], as[na > 2 ? 2 : 0]));
+    return true;
+  }
+
   double gcv(const Level<T>& L, int solver, bool weighted, bool shifted) {
     if (go.gamma_fixed > 0) return go.gamma_fixed;
+    if (!ctx->profiling) return gcv_impl(L, solver, weighted, shifted);
+    const auto t0 = std::chrono::steady_clock::now();
+    const double g = gcv_impl(L, solver, weighted, shifted);
+    ctx->gcv_ns.fetch_add((uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                              std::chrono::steady_clock::now() - t0).count(), std::memory_order_relaxed);
+    return g;
+  }
+
+  double gcv_impl(const Level<T>& L, int solver, bool weighted, bool shifted) {
     ctx->n_gcv.fetch_add(1, std::memory_order_relaxed);
     const size_t n = L.n;
     const int m = L.m;
@@ -835,12 +993,19 @@ struct Engine {
       if (2 * k > kcap || k >= (int)n) break;
     }
     const int ktop = seq.back();
-    // G_D, g_D of cached columns for the current weights and shift
-    for (int j = 0; j < std::min(ktop, cached); ++j) {
+    // G_D, g_D of cached columns for the current weights and shift, GDB_NB
+    // columns per launch (the chunk size is the one the Krylov kernels use)
+    const int ncached = std::min(ktop, cached);
+    for (int j0 = 0; j0 < ncached; j0 += GDB_NB) {
+      const int nb = std::min(GDB_NB, ncached - j0);
+      const size_t need = (size_t)(j0 + nb + 1) * nb * nch;
+      REQUIRE(need <= gpart2_cap, "Gram partial buffer too small");
+      const size_t smb = (size_t)nb * E * VCH_THREADS * sizeof(float);
+      if (smb > 48 * 1024) CK(cudaFuncSetAttribute(k_gram_dcols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
       count_launch();
-      k_gram_col<T><<<nch, VCH_THREADS, 0, st>>>(m, j, V + (size_t)j * n, j, V, nullptr, wx, wy, atbf, dtcf, gpart2,
-                                                 cnt, gGA, gGD, ld, ggA, ggD, E);
+      k_gram_dcols<T><<<nch, VCH_THREADS, smb, st>>>(m, j0, nb, V, wx, wy, dtcf, gpart2, cnt, gGD, ld, ggD, E);
     }
+    CK(cudaGetLastError());
     // new columns: v_j = t / ||t|| (written by the A pass), z = A v_j, t = A^T z
     while (C.kc_cols < ktop) {
       const int j = C.kc_cols;
@@ -1059,7 +1224,7 @@ struct BatchSolver {
     }
     tot += (size_t)workers_for(count) * GcvBufs<Acc>::bytes(n0max, Engine<T>::gram_dim(g), g.exact_max_pixels, 160);
     tot += (size_t)count * (sizeof(LsqrProb<T, Acc>) + sizeof(LsqrState) + sizeof(LsqrCoef<Acc>) + 4 * 256 + 64);
-    tot += tiles * (3 * sizeof(double) + sizeof(int)) + (16ull << 20);
+    tot += tiles * (6 * sizeof(double) + sizeof(int)) + (16ull << 20);
     return tot;
   }
 
@@ -1075,7 +1240,7 @@ struct BatchSolver {
     d_states = A.take<LsqrState>(max_probs);
     d_coefs = A.take<LsqrCoef<Acc>>(max_probs);
     d_tile_prob = A.take<int>(max_tiles + 1);
-    d_part = A.take<double>(3 * max_tiles + 3);
+    d_part = A.take<double>(6 * max_tiles + 6);   // LSQR tile partials, two phase buffers
     d_gb = A.take<GridBarrier>(1);
     d_rc = A.take<double>(2 * (size_t)max_probs);
     P.resize(max_probs);
@@ -1197,26 +1362,19 @@ struct BatchSolver {
     const int np = (int)act.size();
     CK(cudaMemcpyAsync(d_probs, hp.data(), sizeof(LsqrProb<T, Acc>) * np, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_tile_prob, tp.data(), sizeof(int) * tp.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(d_states, 0, sizeof(LsqrState) * np, st));
-    CK(cudaMemsetAsync(d_coefs, 0, sizeof(LsqrCoef<Acc>) * np, st));
-    CK(cudaMemsetAsync(d_gb, 0, sizeof(GridBarrier), st));
     LsqrCtl c;
     c.atol = o.lsqr_atol; c.btol = o.lsqr_btol; c.conlim = o.lsqr_conlim; c.maxit = o.lsqr_maxit;
     c.nprob = np; c.ntiles = (int)tp.size();
     c.tile_prob = d_tile_prob; c.part = d_part; c.cnt = nullptr; c.st = d_states; c.gb = d_gb; c.coef = d_coefs;
     c.limit_ns = 2000000000ull;
-    auto kfn = k_lsqr<T, Acc>;
-    if (sm > 48 * 1024) CK(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    int per_sm = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, sm));
-    REQUIRE(per_sm >= 1, "LSQR kernel does not fit on an SM");
-    const int grid = std::max(1, std::min((int)tp.size(), per_sm * ctx->nsm));
-    const LsqrProb<T, Acc>* pp = d_probs;
-    void* args[] = {(void*)&pp, (void*)&c};
-    if (ctx->profiling) CK(cudaEventRecord(ctx->ev0, st));
-    count_launch();
-    CK(cudaLaunchCooperativeKernel((const void*)kfn, dim3(grid), dim3(32, TY), args, sm, st));
-    if (ctx->profiling) CK(cudaEventRecord(ctx->ev1, st));
+    std::vector<BandOp<Acc>> ops(np);
+    for (int j = 0; j < np; ++j) ops[j] = hp[j].op;
+    auto reset = [&]() {
+      CK(cudaMemsetAsync(d_states, 0, sizeof(LsqrState) * np, st));
+      CK(cudaMemsetAsync(d_coefs, 0, sizeof(LsqrCoef<Acc>) * np, st));
+      CK(cudaMemsetAsync(d_gb, 0, sizeof(GridBarrier), st));
+    };
+    const float lsqr_ms = lsqr_run<T, Acc>(ctx, st, d_probs, c, (int)tp.size(), sm, ops.data(), np, d_gb, reset);
     std::vector<LsqrState> S(np);
     GridBarrier gbh;
     CK(cudaMemcpyAsync(S.data(), d_states, sizeof(LsqrState) * np, cudaMemcpyDeviceToHost, st));
@@ -1232,11 +1390,7 @@ struct BatchSolver {
       if (q.solver == DB_IRLS) ctx->stats.lsqr_pixel_iters_irls += pix;
       else ctx->stats.lsqr_pixel_iters_other += pix;
     }
-    if (ctx->profiling) {
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
-      ctx->stats.lsqr_ms += ms;
-    }
+    if (ctx->profiling) ctx->stats.lsqr_ms += lsqr_ms;
   }
 
   // One scheduler step: one outer iteration of every unfinished problem.
@@ -1350,11 +1504,18 @@ extern "C" db_status db_set_profiling(db_context* c, int on) {
   }
 }
 
+extern "C" db_status db_set_autotune(db_context* c, int on) {
+  if (!c) return DB_EINVAL;
+  c->autotune = on ? 1 : 0;
+  return DB_OK;
+}
+
 extern "C" db_status db_get_stats(db_context* c, db_stats* out) {
   if (!c || !out) return DB_EINVAL;
   *out = c->stats;
   out->kernel_launches = c->n_launches.load();
   out->gcv_calls = c->n_gcv.load();
+  out->gcv_ms = (double)c->gcv_ns.load() * 1e-6;
   return DB_OK;
 }
 
@@ -1363,6 +1524,7 @@ extern "C" db_status db_reset_stats(db_context* c) {
   c->stats = db_stats{};
   c->n_launches = 0;
   c->n_gcv = 0;
+  c->gcv_ns = 0;
   return DB_OK;
 }
 
@@ -1373,8 +1535,7 @@ extern "C" db_status db_context_destroy(db_context* c) {
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->psf_fr) cudaFree(c->psf_fr);
   if (c->psf_fc) cudaFree(c->psf_fc);
-  if (c->arena.base) cudaFree(c->arena.base);
-  delete c;
+  delete c;   // the arena frees its own block
   return DB_OK;
 }
 
@@ -2157,7 +2318,7 @@ static void static_lsqr(cudaStream_t st, const double* psf_host, int S, int m, d
   // barrier must start at zero
   const int nt = L.ntiles_side();
   const int ntiles = nt * nt;
-  double* d_part = cur.take<double>((size_t)std::max(ntiles * 3 + 64, 2 * 8 * nsm));
+  double* d_part = cur.take<double>((size_t)std::max(ntiles * 6 + 64, 2 * 8 * nsm));
   unsigned* d_cnt = cur.take<unsigned>(64);
   double* d_box = cur.take<double>(64);
   GridBarrier* d_gb = cur.take<GridBarrier>(1);
@@ -2189,10 +2350,13 @@ static void static_lsqr(cudaStream_t st, const double* psf_host, int S, int m, d
   c.nprob = 1; c.ntiles = ntiles;
   c.tile_prob = d_tile_prob; c.part = d_part; c.cnt = d_cnt; c.st = d_st; c.gb = d_gb; c.coef = d_coef;
   c.limit_ns = 2000000000ull;
+  c.band_cache = 0;
+  c.band_pw = 0;
+  c.cache_off = 0;
   TileGeom g0 = tile_geom(P.op, false), g1 = tile_geom(P.op, true);
   const int sm = std::max(tile_smem_elems(g0.H, g0.w), tile_smem_elems(g1.H, g1.w)) * (int)sizeof(Acc);
   auto kfn = k_lsqr<T, Acc>;
-  if (sm > 48 * 1024) CK(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   int per_sm = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, sm));
   REQUIRE(per_sm >= 1, "LSQR kernel does not fit on an SM");

@@ -21,6 +21,7 @@
 //    (golden section + parabolic steps, Brent 1973) on log10(gamma).
 #pragma once
 #include "outer.cuh"
+#include <cooperative_groups.h>
 
 namespace db {
 
@@ -222,10 +223,7 @@ __global__ void __launch_bounds__(VCH_THREADS) k_vchunk(size_t n, int nrows, con
   const int r1 = (mode & VCH_NORM) ? nrows + 1 : nrows;
   for (int r = r0 + tid; r < r1; r += VCH_THREADS) {
     float hi = 0.f, lo = 0.f;
-    for (int c = 0; c < nch; ++c) {
-      const float2 pv = __ldcg(&part[(size_t)r * nch + c]);
-      df_add(hi, lo, pv.x, pv.y);
-    }
+    df_sum_loads(part + (size_t)r * nch, nch, hi, lo);
     const double v = (double)hi + (double)lo;
     if (r < nrows) out[(size_t)r * ostride] = v; else *outnorm = v;
   }
@@ -303,10 +301,7 @@ __global__ void __launch_bounds__(VCH_THREADS) k_gram_col(int m, int nr, const f
     const bool a_part = (sidx & 1) == 0;
     if (a_part && !with_a) continue;
     float hi = 0.f, lo = 0.f;
-    for (int c = 0; c < nch; ++c) {
-      const float2 pv = __ldcg(&part[(size_t)sidx * nch + c]);
-      df_add(hi, lo, pv.x, pv.y);
-    }
+    df_sum_loads(part + (size_t)sidx * nch, nch, hi, lo);
     const double v = (double)hi + (double)lo;
     if (i < nrows) {
       const int row = i < nr ? i : jout;
@@ -314,6 +309,90 @@ __global__ void __launch_bounds__(VCH_THREADS) k_gram_col(int m, int nr, const f
     } else {
       if (a_part) gA[jout] = v; else gD[jout] = v;
     }
+  }
+  if (tid == 0) *cnt = 0;
+}
+
+// D part of nb Gram columns at once (the basis is cached, so G_A is known):
+// for the columns j = j0 .. j0+nb-1, with y_j = L^T diag(w^2) L v_j computed
+// here, GD[i*ld + j] = V_i . y_j for i <= j and gD[j] = dtc . v_j (dtc may be
+// null -> 0). Each chunk of V is read once for all nb columns. part needs
+// (j0 + nb + 1) * nb * gridDim.x float2.
+constexpr int GDB_NB = 8;
+template <typename T>
+__global__ void __launch_bounds__(VCH_THREADS) k_gram_dcols(int m, int j0, int nb, const float* __restrict__ V,
+    const T* __restrict__ wx, const T* __restrict__ wy, const float* __restrict__ dtc, float2* __restrict__ part,
+    unsigned* cnt, double* GD, int ld, double* gD, int E) {
+  extern __shared__ __align__(16) float ysm[];          // [nb][E * VCH_THREADS]
+  __shared__ int s_last;
+  const size_t n = (size_t)m * m;
+  const int nch = gridDim.x, ch = blockIdx.x;
+  const int CH = E * VCH_THREADS;
+  const size_t beg = (size_t)ch * CH;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = VCH_THREADS / 32;
+  auto W = [&](const T* p, size_t q) -> float { return p ? (float)to_acc(p[q]) : 1.f; };
+  for (int c = 0; c < nb; ++c) {
+    const float* vj = V + (size_t)(j0 + c) * n;
+    for (int k = 0; k < E; ++k) {
+      const int le = k * VCH_THREADS + tid;
+      const size_t i = beg + le;
+      float yv = 0.f;
+      if (i < n) {
+        const int r = (int)(i % m), cc = (int)(i / m);
+        const float xv = vj[i];
+        if (r < m - 1) { const float w = W(wx, i); yv -= w * w * (vj[i + 1] - xv); }
+        if (r > 0) { const float w = W(wx, i - 1); yv += w * w * (xv - vj[i - 1]); }
+        if (cc < m - 1) { const float w = W(wy, i); yv -= w * w * (vj[i + m] - xv); }
+        if (cc > 0) { const float w = W(wy, i - m); yv += w * w * (xv - vj[i - m]); }
+      }
+      ysm[(size_t)c * CH + le] = yv;
+    }
+  }
+  __syncthreads();
+  const int j1 = j0 + nb;               // rows 0 .. j1-1, then the g_D row
+  for (int i = wid; i <= j1; i += nw) {
+    float a[GDB_NB], cmp[GDB_NB];
+#pragma unroll
+    for (int c = 0; c < GDB_NB; ++c) { a[c] = 0.f; cmp[c] = 0.f; }
+    const bool grow = (i == j1);
+    const float* vi = grow ? dtc : V + (size_t)i * n;
+    if (!(grow && !dtc)) {
+      for (int le = lane; le < CH; le += 32) {
+        if (beg + le >= n) break;
+        const float vv = vi[beg + le];
+#pragma unroll
+        for (int c = 0; c < GDB_NB; ++c) {
+          if (c >= nb) break;
+          const float q = grow ? V[(size_t)(j0 + c) * n + beg + le] : ysm[(size_t)c * CH + le];
+          const float y = vv * q - cmp[c], t = a[c] + y;
+          cmp[c] = (t - a[c]) - y;
+          a[c] = t;
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < GDB_NB; ++c) {
+      if (c >= nb) break;
+      const float2 r = warp_df(a[c], cmp[c]);
+      if (lane == 0) part[((size_t)i * nb + c) * nch + ch] = r;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = (atomicAdd(cnt, 1u) == (unsigned)nch - 1);
+    __threadfence();
+  }
+  __syncthreads();
+  if (!s_last) return;
+  for (int sidx = tid; sidx < (j1 + 1) * nb; sidx += VCH_THREADS) {
+    const int i = sidx / nb, c = sidx - (sidx / nb) * nb;
+    const int j = j0 + c;
+    if (i < j1 && i > j) continue;      // lower triangle: not stored
+    float hi = 0.f, lo = 0.f;
+    df_sum_loads(part + (size_t)sidx * nch, nch, hi, lo);
+    const double v = (double)hi + (double)lo;
+    if (i < j1) GD[(size_t)i * ld + j] = v; else gD[j] = v;
   }
   if (tid == 0) *cnt = 0;
 }
@@ -776,10 +855,7 @@ __global__ void __launch_bounds__(256) k_trace_table(const float* __restrict__ r
   if (!s_last) return;
   for (int j = threadIdx.x; j < npts; j += blockDim.x) {
     float h = 0.f, l = 0.f;
-    for (int b = 0; b < nb; ++b) {
-      const float2 pv = __ldcg(&part[(size_t)j * nb + b]);
-      df_add(h, l, pv.x, pv.y);
-    }
+    df_sum_loads(part + (size_t)j * nb, nb, h, l);
     tab[j] = (double)h + (double)l;
   }
   if (threadIdx.x == 0) *cnt = 0;
@@ -1071,6 +1147,390 @@ __global__ void __launch_bounds__(SEL_THREADS) k_gcv_select(GcvSelectArgs a0, Gc
   double B = tgrid(jbest < npts - 1 ? jbest + 1 : npts - 1);
   // Brent (golden section + parabolic interpolation); every thread runs the
   // same control flow on the same values.
+  const double cgold = 0.5 * (3.0 - sqrt(5.0));
+  const double sqeps = sqrt(2.220446049250313e-16);
+  double x = A + cgold * (B - A), w = x, v = x;
+  double fx = feval(x), fw = fx, fv = fx;
+  double d = 0.0, e = 0.0;
+  for (int nfev = 1; nfev < 500; ++nfev) {
+    const double xm = 0.5 * (A + B);
+    const double tol1 = sqeps * fabs(x) + a.tolx / 3.0;
+    const double tol2 = 2.0 * tol1;
+    if (fabs(x - xm) <= tol2 - 0.5 * (B - A)) break;
+    bool golden = true;
+    if (fabs(e) > tol1) {
+      double r = (x - w) * (fx - fv);
+      double q = (x - v) * (fx - fw);
+      double pp = (x - v) * q - (x - w) * r;
+      q = 2.0 * (q - r);
+      if (q > 0.0) pp = -pp;
+      q = fabs(q);
+      const double etemp = e;
+      e = d;
+      if (fabs(pp) < fabs(0.5 * q * etemp) && pp > q * (A - x) && pp < q * (B - x)) {
+        d = pp / q;
+        const double uu = x + d;
+        if ((uu - A) < tol2 || (B - uu) < tol2) d = (xm >= x) ? tol1 : -tol1;
+        golden = false;
+      }
+    }
+    if (golden) { e = (x < xm) ? (B - x) : (A - x); d = cgold * e; }
+    const double uu = (fabs(d) >= tol1) ? x + d : x + (d > 0 ? tol1 : -tol1);
+    const double fu = feval(uu);
+    if (fu <= fx) {
+      if (uu < x) B = x; else A = x;
+      v = w; fv = fw; w = x; fw = fx; x = uu; fx = fu;
+    } else {
+      if (uu < x) A = uu; else B = uu;
+      if (fu <= fw || w == x) { v = w; fv = fw; w = uu; fw = fu; }
+      else if (fu <= fv || v == x || v == w) { v = uu; fv = fu; }
+    }
+  }
+  const double tbest = (fx <= fbest) ? x : tgrid(jbest);
+  if (tid == 0) {
+    a.out[0] = pow(10.0, tbest);
+    a.out[1] = (double)ext;
+    a.out[2] = (fx <= fbest) ? fx : fbest;
+  }
+}
+
+// ---- the selection on a thread-block cluster ---------------------------------
+// The same computation as k_gcv_select for one projected-mode selection,
+// spread over a cluster of SCL_NC CTAs (one per SM), since one SM issues only
+// about two FP64 FMAs per clock. Row i of the working matrices belongs to
+// CTA i % SCL_NC.
+//  * Cholesky, right-looking: per column, every CTA sends its rows' entries
+//    to all CTAs (distributed shared memory), and every CTA forms the same
+//    column of R and updates its own rows; so every CTA ends with a full
+//    copy of R (packed lower triangle).
+//  * X = R^{-1} [G_A | g_A | g_D] and C = R^{-1} X^T: each CTA solves its own
+//    columns (right-looking over the rows of R, its local copy), X passing
+//    through global memory between the two; column q of C is row q, so each
+//    CTA ends with its own rows of C (full rows).
+//  * Householder: per step, the column below the diagonal is gathered from
+//    the row owners and the product C u is summed from per-CTA partials (in
+//    CTA order); every CTA then forms the same u, w, K and updates its rows.
+//  * T's diagonals and p_A, p_D are gathered; the rest (w0, grid, Brent)
+//    runs in CTA 0 alone, the others having left once no remote access
+//    remains.
+// Every value that more than one CTA computes is computed from the same data
+// in the same order, so the copies agree bit for bit.
+constexpr int SCL_NC = 8;
+constexpr int SCL_THREADS = 256;
+constexpr int SCL_MAXK = 164;
+
+struct SclLayout {
+  int K, nrl, ncl;
+  size_t rp, mr, xc, vec, cb, pb, sc, total;   // offsets in doubles
+};
+__host__ __device__ inline SclLayout scl_layout(int K) {
+  SclLayout L;
+  L.K = K;
+  L.nrl = (K + SCL_NC - 1) / SCL_NC;
+  L.ncl = (K + 2 + SCL_NC - 1) / SCL_NC;
+  L.rp = 0;
+  L.mr = L.rp + (size_t)K * (K + 1) / 2;
+  L.xc = L.mr + (size_t)L.nrl * K;
+  L.vec = L.xc + (size_t)K * L.ncl;
+  L.cb = L.vec + (size_t)12 * K;
+  L.pb = L.cb + (size_t)2 * K;
+  L.sc = L.pb + (size_t)SCL_NC * K;
+  L.total = L.sc + (size_t)2 * SCL_NC * 4;
+  return L;
+}
+__host__ __device__ inline size_t rp_at(int i, int j) { return (size_t)i * (i + 1) / 2 + j; }
+
+// In-place forward substitution R x = rhs on nc columns held as
+// Xc[i * nc + c] (R from the packed copy, rdiag = 1 / diag R), right-looking
+// over the rows so every step is parallel over (row, column).
+__device__ void scl_forward(int K, int nc, const double* Rp, const double* rdiag, double* Xc) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = 0; i < K; ++i) {
+    if (tid < nc) Xc[(size_t)i * nc + tid] *= rdiag[i];
+    __syncthreads();
+    const int rows = K - i - 1;
+    for (int idx = tid; idx < rows * nc; idx += nth) {
+      const int i2 = i + 1 + idx / nc, c = idx - (idx / nc) * nc;
+      Xc[(size_t)i2 * nc + c] -= Rp[rp_at(i2, i)] * Xc[(size_t)i * nc + c];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(SCL_THREADS) k_gcv_select_cl(GcvSelectArgs a0, GcvSelectArgs a1, GcvSelectArgs a2) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) double sdyn[];
+  __shared__ double sh[32 * 3];
+  __shared__ double s_gam[SEL_MAXPTS], s_tr[SEL_MAXPTS], s_f[SEL_MAXPTS];
+  __shared__ double s_bc[4];
+  const int sel = blockIdx.x / SCL_NC;
+  GcvSelectArgs a = a0;
+  if (sel == 1) a = a1;
+  else if (sel == 2) a = a2;
+  const int rank = (int)cl.block_rank();
+  const int K = a.kk, ld = a.ld, tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nwarp = nth >> 5;
+  const SclLayout Ly = scl_layout(K);
+  const int nrl = Ly.nrl, ncl = Ly.ncl;
+  double* Rp = sdyn + Ly.rp;
+  double* Mr = sdyn + Ly.mr;      // own rows: M during Cholesky, then C
+  double* Xc = sdyn + Ly.xc;      // own columns (X, then C)
+  double* pA = sdyn + Ly.vec;
+  double* pD = pA + K;
+  double* dg = pD + K;
+  double* eo = dg + K;
+  double* u = eo + K;
+  double* p = u + K;
+  double* fvec = p + K;
+  double* rdiag = fvec + K;
+  double* colc = rdiag + K;
+  double* wk3 = colc + K;         // 3 K, scratch of the trial-gamma solves
+  double* cbuf = sdyn + Ly.cb;    // 2 K, double-buffered column exchange
+  double* pbuf = sdyn + Ly.pb;    // SCL_NC x K partial products
+  double* scbuf = sdyn + Ly.sc;   // 2 x SCL_NC x 4 partial scalars (double-buffered)
+  double* Xg = a.work;            // K x K, X through global memory
+  double* vg = Xg + (size_t)K * K;            // p_A, p_D through global memory (2 K)
+  double* scratch = vg + 2 * (size_t)K;       // grid Thomas scratch, 2 K per point
+  auto mapk = [&](int i) { return (a.kshift >= 0 && i == K - 1) ? a.kshift : i; };
+  auto GAe = [&](int i, int j) {
+    i = mapk(i); j = mapk(j);
+    return i <= j ? a.GA[(size_t)i * ld + j] : a.GA[(size_t)j * ld + i];
+  };
+  auto GDe = [&](int i, int j) {
+    i = mapk(i); j = mapk(j);
+    return i <= j ? a.GD[(size_t)i * ld + j] : a.GD[(size_t)j * ld + i];
+  };
+  // 1. own rows of M = G_A + G_D (lower part); the pivot floor from the full diagonal
+  for (int li = wid; li < nrl; li += nwarp) {
+    const int i = rank + li * SCL_NC;
+    if (i >= K) continue;
+    for (int j = lane; j <= i; j += 32) Mr[(size_t)li * K + j] = GAe(i, j) + GDe(i, j);
+  }
+  if (tid == 0) {
+    double md = 0.0;
+    for (int i = 0; i < K; ++i) md = fmax(md, GAe(i, i) + GDe(i, i));
+    s_bc[0] = md;
+  }
+  __syncthreads();
+  const double piv_floor = 1e-14 * s_bc[0];
+  cl.sync();   // every CTA of the cluster is running before the first remote store
+  // 2. Cholesky M = R R^T, column by column
+  for (int c = 0; c < K; ++c) {
+    double* cb = cbuf + (size_t)(c & 1) * K;
+    for (int idx = tid; idx < nrl * SCL_NC; idx += nth) {
+      const int li = idx / SCL_NC, r = idx - li * SCL_NC;
+      const int i = rank + li * SCL_NC;
+      if (i >= c && i < K) cl.map_shared_rank(cb, r)[i] = Mr[(size_t)li * K + c];
+    }
+    cl.sync();
+    if (tid == 0) {
+      const double piv = cb[c];
+      const double pv = piv > piv_floor ? piv : piv_floor;
+      const double ir = rsqrt_d(pv);
+      rdiag[c] = ir;
+      Rp[rp_at(c, c)] = pv * ir;
+    }
+    __syncthreads();
+    const double ir = rdiag[c];
+    for (int i = c + 1 + tid; i < K; i += nth) {
+      const double v = cb[i] * ir;
+      Rp[rp_at(i, c)] = v;
+      colc[i] = v;
+    }
+    __syncthreads();
+    for (int li = wid; li < nrl; li += nwarp) {
+      const int i = rank + li * SCL_NC;
+      if (i <= c || i >= K) continue;
+      const double ci = colc[i];
+      double* Mi = Mr + (size_t)li * K;
+      for (int j = c + 1 + lane; j <= i; j += 32) Mi[j] -= ci * colc[j];
+    }
+    __syncthreads();
+  }
+  // 3. X = R^{-1} [G_A | g_A | g_D], own columns q = rank + lq * SCL_NC
+  for (int idx = tid; idx < K * ncl; idx += nth) {
+    const int i = idx / ncl, lq = idx - (idx / ncl) * ncl;
+    const int q = rank + lq * SCL_NC;
+    double v = 0.0;
+    if (q < K) v = GAe(i, q);
+    else if (q == K) v = a.gA[mapk(i)];
+    else if (q == K + 1) v = a.gD[mapk(i)];
+    Xc[(size_t)i * ncl + lq] = v;
+  }
+  __syncthreads();
+  scl_forward(K, ncl, Rp, rdiag, Xc);
+  for (int idx = tid; idx < K * ncl; idx += nth) {
+    const int i = idx / ncl, lq = idx - (idx / ncl) * ncl;
+    const int q = rank + lq * SCL_NC;
+    const double v = Xc[(size_t)i * ncl + lq];
+    if (q < K) Xg[(size_t)i * K + q] = v;
+    else if (q == K) vg[i] = v;
+    else if (q == K + 1) vg[K + i] = v;
+  }
+  cl.sync();
+  for (int i = tid; i < K; i += nth) { pA[i] = __ldcg(vg + i); pD[i] = __ldcg(vg + K + i); }
+  // 4. C = R^{-1} X^T, own columns q (= own rows, C being symmetric)
+  const int ncc = nrl;
+  for (int idx = tid; idx < K * ncc; idx += nth) {
+    const int i = idx / ncc, lq = idx - (idx / ncc) * ncc;
+    const int q = rank + lq * SCL_NC;
+    Xc[(size_t)i * ncc + lq] = q < K ? __ldcg(Xg + (size_t)q * K + i) : 0.0;
+  }
+  __syncthreads();
+  scl_forward(K, ncc, Rp, rdiag, Xc);
+  for (int idx = tid; idx < K * ncc; idx += nth) {
+    const int i = idx / ncc, lq = idx - (idx / ncc) * ncc;
+    Mr[(size_t)lq * K + i] = Xc[(size_t)i * ncc + lq];
+  }
+  __syncthreads();
+  // 5. Householder tridiagonalisation on the distributed rows
+  for (int k = 0; k + 2 < K; ++k) {
+    const int len = K - k - 1;
+    double* xb = cbuf + (size_t)(k & 1) * K;
+    double* scb = scbuf + (size_t)(k & 1) * SCL_NC * 4;
+    double nx[1] = {0.0};
+    for (int li = tid; li < nrl; li += nth) {
+      const int i = rank + li * SCL_NC;
+      if (i > k && i < K) { const double v = Mr[(size_t)li * K + k]; nx[0] += v * v; }
+    }
+    sel_sumN<1>(nx, nrl, sh);
+    for (int idx = tid; idx < nrl * SCL_NC; idx += nth) {
+      const int li = idx / SCL_NC, r = idx - li * SCL_NC;
+      const int i = rank + li * SCL_NC;
+      if (i > k && i < K) cl.map_shared_rank(xb, r)[i] = Mr[(size_t)li * K + k];
+    }
+    if (tid < SCL_NC) cl.map_shared_rank(scb, tid)[rank * 4] = nx[0];
+    cl.sync();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int r = 0; r < SCL_NC; ++r) t += scb[r * 4];
+      s_bc[0] = t;
+    }
+    __syncthreads();
+    const double nx2 = s_bc[0];
+    const double x0 = xb[k + 1];
+    if (nx2 - x0 * x0 <= 1e-300 * (1.0 + nx2)) continue;   // already reduced: identical in every CTA
+    if (tid == 0) {
+      const double inx = rsqrt_d(nx2);
+      const double nrm = nx2 * inx;
+      const double alpha = x0 >= 0 ? -nrm : nrm;
+      s_bc[1] = alpha;
+      s_bc[2] = rsqrt_d(2.0 * nrm * (nrm + fabs(x0)));
+    }
+    __syncthreads();
+    const double alpha = s_bc[1], inv_nu = s_bc[2];
+    for (int j = tid; j < len; j += nth) u[j] = (xb[k + 1 + j] - (j == 0 ? alpha : 0.0)) * inv_nu;
+    __syncthreads();
+    // partial p_j = sum over own rows i > k of C[i][k+1+j] u_{i-k-1}, sent to every CTA
+    for (int j = tid; j < len; j += nth) {
+      double acc = 0.0;
+      for (int li = 0; li < nrl; ++li) {
+        const int i = rank + li * SCL_NC;
+        if (i > k && i < K) acc += Mr[(size_t)li * K + k + 1 + j] * u[i - k - 1];
+      }
+      for (int r = 0; r < SCL_NC; ++r) cl.map_shared_rank(pbuf, r)[(size_t)rank * K + j] = acc;
+    }
+    cl.sync();
+    for (int j = tid; j < len; j += nth) {
+      double t = 0.0;
+      for (int r = 0; r < SCL_NC; ++r) t += pbuf[(size_t)r * K + j];
+      p[j] = t;
+    }
+    __syncthreads();
+    double kd[3] = {0.0, 0.0, 0.0};
+    for (int j = tid; j < len; j += nth) {
+      kd[0] += u[j] * p[j];
+      kd[1] += u[j] * pA[k + 1 + j];
+      kd[2] += u[j] * pD[k + 1 + j];
+    }
+    sel_sumN<3>(kd, len, sh);
+    const double Kc = kd[0], da = kd[1], dd = kd[2];
+    for (int j = tid; j < len; j += nth) p[j] = 2.0 * p[j] - 2.0 * Kc * u[j];   // w
+    __syncthreads();
+    for (int li = wid; li < nrl; li += nwarp) {
+      const int i = rank + li * SCL_NC;
+      if (i <= k || i >= K) continue;
+      const double ui = u[i - k - 1], wi = p[i - k - 1];
+      double* Mi = Mr + (size_t)li * K + k + 1;
+      for (int j = lane; j < len; j += 32) Mi[j] -= ui * p[j] + wi * u[j];
+    }
+    for (int j = tid; j < len; j += nth) {
+      pA[k + 1 + j] -= 2.0 * da * u[j];
+      pD[k + 1 + j] -= 2.0 * dd * u[j];
+    }
+    if (tid == 0 && (k + 1) % SCL_NC == rank) Mr[(size_t)((k + 1) / SCL_NC) * K + k] = alpha;
+    __syncthreads();
+  }
+  // 6. T's diagonals from the row owners
+  for (int li = tid; li < nrl; li += nth) {
+    const int i = rank + li * SCL_NC;
+    if (i >= K) continue;
+    const double dv = Mr[(size_t)li * K + i];
+    const double ev = i > 0 ? Mr[(size_t)li * K + i - 1] : 0.0;   // T[i][i-1] = eo[i-1]
+    for (int r = 0; r < SCL_NC; ++r) {
+      cl.map_shared_rank(dg, r)[i] = dv;
+      if (i > 0) cl.map_shared_rank(eo, r)[i - 1] = ev;
+    }
+  }
+  if (tid == 0) eo[K - 1] = 0.0;
+  cl.sync();
+  // no remote access follows: the rest runs in CTA 0 alone
+  if (rank != 0) return;
+  // 7. w0 = T^{-1} p_A, f = p_A + p_D - w0, r0^2 (one Thomas sweep)
+  if (tid == 0) {
+    sel_tri_solve(K, dg, eo, pA, 0.0, p, u, 0.0);
+    double pw = 0.0;
+    for (int i = 0; i < K; ++i) {
+      pw += pA[i] * u[i];
+      fvec[i] = pA[i] + pD[i] - u[i];
+    }
+    s_bc[3] = pw;
+  }
+  __syncthreads();
+  const double r02 = (a.bnorm2 - s_bc[3]) > 0.0 ? (a.bnorm2 - s_bc[3]) : 0.0;
+  // 8. grid search with widening, then Brent (as k_gcv_select, in every CTA)
+  const int npts = a.npts < SEL_MAXPTS ? a.npts : SEL_MAXPTS;
+  double lo = a.lo, hi = a.hi;
+  int ext = 0, jbest = 0;
+  double fbest = 0.0, step = 0.0;
+  double* lam = nullptr;
+  for (;;) {
+    step = (hi - lo) / (npts - 1);
+    for (int j = tid; j < npts; j += nth) s_gam[j] = pow(10.0, (j == npts - 1) ? hi : lo + j * step);
+    __syncthreads();
+    if (ext == 0 && a.trace_tab) {
+      for (int j = tid; j < npts; j += nth) s_tr[j] = a.trace_tab[j];
+      __syncthreads();
+    } else {
+      sel_traces(a, lam, npts, s_gam, s_tr, sh);
+    }
+    for (int j = tid; j < npts; j += nth) {
+      double* sc2 = scratch + (size_t)j * 2 * K;
+      const double num = sel_numerator(K, dg, eo, fvec, r02, s_gam[j], sc2, sc2 + K);
+      const double den = a.n - s_tr[j];
+      s_f[j] = num / (den * den);
+    }
+    __syncthreads();
+    jbest = 0;
+    fbest = s_f[0];
+    for (int j = 1; j < npts; ++j)
+      if (s_f[j] < fbest) { fbest = s_f[j]; jbest = j; }
+    __syncthreads();
+    if (jbest == 0 && ext < a.max_ext) { lo -= 4.0; ++ext; continue; }
+    if (jbest == npts - 1 && ext < a.max_ext) { hi += 4.0; ++ext; continue; }
+    break;
+  }
+  auto tgrid = [&](int j) { return (j == npts - 1) ? hi : lo + j * step; };
+  auto feval = [&](double t) -> double {
+    const double gam = pow(10.0, t);
+    const double num = sel_eval(a, K, dg, eo, fvec, r02, lam, gam, u, wk3, sh, &s_bc[2]);
+    const double den = a.n - s_bc[2];
+    __syncthreads();
+    return num / (den * den);
+  };
+  double A = tgrid(jbest > 0 ? jbest - 1 : 0);
+  double B = tgrid(jbest < npts - 1 ? jbest + 1 : npts - 1);
   const double cgold = 0.5 * (3.0 - sqrt(5.0));
   const double sqeps = sqrt(2.220446049250313e-16);
   double x = A + cgold * (B - A), w = x, v = x;

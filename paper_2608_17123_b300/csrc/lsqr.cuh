@@ -59,6 +59,9 @@ struct LsqrCtl {
   void* coef;                    // [nprob] LsqrCoef<Acc>
   GridBarrier* gb;
   unsigned long long limit_ns;
+  int band_cache;                // 1: band rows of the cached tiles kept in shared memory (one-term PSFs)
+  int band_pw;                   // row pitch of the band cache (Acc elements)
+  int cache_off;                 // offset of the band cache in dynamic shared memory (Acc elements)
 };
 
 template <typename T>
@@ -76,6 +79,8 @@ __device__ __forceinline__ LsqrState load_state(const LsqrState* s) {
   for (int k = 0; k < 4; ++k) oi[k] = __ldcg(di + k);
   return r;
 }
+
+__device__ int lsqr_wait_release(const LsqrCtl& ctl, int ph);
 
 // Loads of one tile issued before any of them is used: the problem's done
 // flag and coefficients, the pointwise operands of this thread's pixels, the
@@ -104,8 +109,8 @@ __device__ __forceinline__ TileHead<Acc> load_head(const LsqrCtl& ctl, int p) {
 
 // Returns false (nothing written) when the problem has already stopped.
 template <typename T, typename Acc>
-__device__ bool lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p, bool init, bool first,
-                            int r0, int c0, Acc* sm, Acc (&red)[3]) {
+__device__ int lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p, bool init, bool first,
+                           int r0, int c0, Acc* sm, Acc (&red)[3], Acc* cbr, Acc* cbc, int ph, bool wait_rel) {
   const int m = P.m;
   const TileGeom g = tile_geom(P.op, false);
   Acc* sx = sm;
@@ -113,14 +118,13 @@ __device__ bool lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p
   Acc* sbr = sz + g.H * TM;
   Acc* sbc = sbr + TM * band_pitch(g.w);
   const T* src = init ? P.x0 : P.v;
-  const TileHead<Acc> h = load_head<Acc>(ctl, p);
   const bool wtd = (P.solver == 0);
   Acc pu[PIX], px[PIX], py[PIX], pw_[PIX], pd[PIX], wx[PIX], wy[PIX];
   {
     const int rr = r0 + threadIdx.x;
 #pragma unroll
     for (int j = 0; j < PIX; ++j) {
-      const int cc = c0 + threadIdx.y + TY * j;
+      const int cc = c0 + pix_col(j);
       pu[j] = px[j] = py[j] = pw_[j] = pd[j] = Acc(0);
       wx[j] = wy[j] = Acc(1);
       if (rr < m && cc < m) {
@@ -137,11 +141,18 @@ __device__ bool lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p
   }
   if (src) {
     gather_tile<true, T, Acc>(src, m, r0, c0, g, Acc(1), sx);
-    load_bands<Acc>(P.op, false, 0, r0, c0, g, sbr, sbc);
+    if (!cbr) load_bands<Acc>(P.op, false, 0, r0, c0, g, sbr, sbc);
   }
-  if (h.done) return false;
   Acc Av[PIX] = {};
-  if (src) tile_conv<Acc>(P.op, false, r0, c0, g, sx, sz, sbr, sbc, Av, true);
+  if (src) tile_conv<Acc>(P.op, false, r0, c0, g, sx, sz, cbr ? cbr : sbr, cbc ? cbc : sbc, Av, true);
+  // the convolution needs the new vectors only; the coefficients and the
+  // stop flag come from the previous phase's scalar update
+  if (wait_rel) {
+    const int d = lsqr_wait_release(ctl, ph);
+    if (d != 0) return d > 0 ? -1 : -2;
+  }
+  const TileHead<Acc> h = load_head<Acc>(ctl, p);
+  if (h.done) return 0;
   const Acc sc = init ? Acc(1) : h.K.inv_alpha;   // v = v~ / alpha
   const Acc sg = P.sg;
   const Acc ab = init ? Acc(0) : h.K.ab;
@@ -151,7 +162,7 @@ __device__ bool lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p
   Acc s_u = 0, s_d = 0, s_w = 0;
 #pragma unroll
   for (int j = 0; j < PIX; ++j) {
-    const int cl = threadIdx.y + TY * j;
+    const int cl = pix_col(j);
     const int c = c0 + cl;
     if (r >= m || c >= m) continue;
     const size_t i = r + (size_t)c * m;
@@ -200,19 +211,18 @@ __device__ bool lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p
   red[0] = s_u;
   red[1] = s_d;
   red[2] = s_w;
-  return true;
+  return 1;
 }
 
 template <typename T, typename Acc>
-__device__ bool lsqr_pass_B(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p, bool init,
-                            int r0, int c0, Acc* sm, Acc (&red)[3]) {
+__device__ int lsqr_pass_B(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p, bool init,
+                           int r0, int c0, Acc* sm, Acc (&red)[3], Acc* cbr, Acc* cbc, int ph, bool wait_rel) {
   const int m = P.m;
   const TileGeom g = tile_geom(P.op, true);
   Acc* sx = sm;
   Acc* sz = sx + g.H * g.H;
   Acc* sbr = sz + g.H * TM;
   Acc* sbc = sbr + TM * band_pitch(g.w);
-  const TileHead<Acc> h = load_head<Acc>(ctl, p);
   const bool wtd = (P.solver == 0);
   // L^T applied to the (unscaled) gradient planes of this thread's pixels, and the old v
   Acc lt[PIX], vo[PIX];
@@ -220,7 +230,7 @@ __device__ bool lsqr_pass_B(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p
     const int rr = r0 + threadIdx.x;
 #pragma unroll
     for (int j = 0; j < PIX; ++j) {
-      const int cc = c0 + threadIdx.y + TY * j;
+      const int cc = c0 + pix_col(j);
       Acc l = 0, v = 0;
       if (rr < m && cc < m) {
         // all loads issued unconditionally (clamped neighbours), then combined
@@ -242,10 +252,15 @@ __device__ bool lsqr_pass_B(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p
     }
   }
   gather_tile<true, T, Acc>(P.uA, m, r0, c0, g, Acc(1), sx);
-  load_bands<Acc>(P.op, true, 0, r0, c0, g, sbr, sbc);
-  if (h.done) return false;
+  if (!cbr) load_bands<Acc>(P.op, true, 0, r0, c0, g, sbr, sbc);
   Acc At[PIX] = {};
-  tile_conv<Acc>(P.op, true, r0, c0, g, sx, sz, sbr, sbc, At, true);
+  tile_conv<Acc>(P.op, true, r0, c0, g, sx, sz, cbr ? cbr : sbr, cbc ? cbc : sbc, At, true);
+  if (wait_rel) {
+    const int d = lsqr_wait_release(ctl, ph);
+    if (d != 0) return d > 0 ? -1 : -2;
+  }
+  const TileHead<Acc> h = load_head<Acc>(ctl, p);
+  if (h.done) return 0;
   const Acc ib = h.K.inv_beta;                    // u = u~ / beta
   const Acc sgb = P.sg * ib;
   const Acc ba = init ? Acc(0) : h.K.ba;
@@ -253,7 +268,7 @@ __device__ bool lsqr_pass_B(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p
   Acc s_v = 0;
 #pragma unroll
   for (int j = 0; j < PIX; ++j) {
-    const int c = c0 + threadIdx.y + TY * j;
+    const int c = c0 + pix_col(j);
     if (r >= m || c >= m) continue;
     const size_t i = r + (size_t)c * m;
     Acc vt = ib * At[j] + sgb * lt[j];
@@ -264,7 +279,7 @@ __device__ bool lsqr_pass_B(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p
   red[0] = s_v;
   red[1] = Acc(0);
   red[2] = Acc(0);
-  return true;
+  return 1;
 }
 
 // Scalar work once every tile of a problem has reported (run by one thread).
@@ -439,30 +454,37 @@ __device__ __forceinline__ void problem_partials<double>(const double* part, int
   for (int k = 0; k < 3; ++k) tot[k] = warp_sum(tot[k]);
 }
 
-// End of a phase: every block has written its tiles' partials. The last block
-// to arrive at the grid barrier reduces every problem's partials (warp w takes
-// problems w, w + 8, ...; fixed order over tiles), runs the scalar updates,
-// decides whether all problems have stopped, and only then releases the
-// others. Returns 0 to continue, 1 when all problems are done, -1 on timeout.
+// Tile partials of phase ph (0, 1, 2, ...): two buffers by phase parity,
+// since blocks write the next phase's partials while the finishing block may
+// still read this phase's.
+__device__ __forceinline__ double* phase_part(const LsqrCtl& ctl, int ph) {
+  return ctl.part + (size_t)(ph & 1) * ctl.ntiles * 3;
+}
+
+// End of phase ph, a barrier in two halves. Every block adds one to a
+// counter that only grows. The block that brings it to G (ph + 1) reduces
+// every problem's partials (warp w takes problems w, w + 8, ...; tile order),
+// runs the scalar updates and publishes them with gen = ph + 1 and the
+// all-stopped decision. Every other block waits only until all blocks have
+// arrived: its next loads and convolution read the new vectors, not the new
+// coefficients, and it meets the publication later (lsqr_wait_release).
+// Returns -1 on timeout.
 template <typename T, typename Acc>
-__device__ int lsqr_phase_end(const LsqrProb<T, Acc>* probs, const LsqrCtl& ctl, LsqrCoef<Acc>* coef, bool isF,
-                              int it) {
-  __shared__ int s_last, s_ok, s_dec, s_live;
-  __shared__ unsigned s_gen;
+__device__ int lsqr_phase_arrive(const LsqrProb<T, Acc>* probs, const LsqrCtl& ctl, LsqrCoef<Acc>* coef, bool isF,
+                                 int it, int ph) {
+  __shared__ int s_last, s_ok, s_live;
   GridBarrier* gb = ctl.gb;
   const int tid = threadIdx.x + 32 * threadIdx.y;
+  const unsigned target = gridDim.x * (unsigned)(ph + 1);
   using aref = cuda::atomic_ref<unsigned, cuda::thread_scope_device>;
   __syncthreads();
   if (tid == 0) {
     s_ok = (*(volatile int*)&gb->error == 0);
     s_last = 0;
     s_live = 0;
-    if (s_ok) {
-      s_gen = aref(gb->gen).load(cuda::memory_order_relaxed);
-      // release: this block's writes of the phase (ordered before by the
-      // block barrier) become visible to whoever acquires the counter
-      s_last = (aref(gb->count).fetch_add(1u, cuda::memory_order_acq_rel) == gridDim.x - 1);
-    }
+    // release: this block's writes of the phase (ordered before by the block
+    // barrier) become visible to whoever acquires the counter
+    if (s_ok) s_last = (aref(gb->count).fetch_add(1u, cuda::memory_order_acq_rel) == target - 1);
   }
   __syncthreads();
   if (!s_ok) return -1;
@@ -474,7 +496,7 @@ __device__ int lsqr_phase_end(const LsqrProb<T, Acc>* probs, const LsqrCtl& ctl,
       LsqrState S;
       if (lane == 0) S = load_state(&ctl.st[p]);
       double tot[3];
-      problem_partials<Acc>(ctl.part + (size_t)P.tile_begin * 3, P.ntiles, tot);
+      problem_partials<Acc>(phase_part(ctl, ph) + (size_t)P.tile_begin * 3, P.ntiles, tot);
       if (lane == 0 && !S.done) {
         const int done = isF ? lsqr_finish_F<Acc>(ctl, S, &ctl.st[p], coef + p, it == 0, it, tot)
                              : lsqr_finish_B<Acc>(S, &ctl.st[p], coef + p, it == 0, tot);
@@ -483,29 +505,49 @@ __device__ int lsqr_phase_end(const LsqrProb<T, Acc>* probs, const LsqrCtl& ctl,
     }
     __syncthreads();
     if (tid == 0) {
-      const int all = s_live ? 0 : 1;
-      gb->decision = all;
-      gb->count = 0;
-      // release: the scalar updates of this block become visible with the new generation
-      aref(gb->gen).fetch_add(1u, cuda::memory_order_release);
-      s_dec = all;
+      gb->decision = s_live ? 0 : 1;
+      // release: the scalar updates of this block become visible with gen
+      aref(gb->gen).store((unsigned)(ph + 1), cuda::memory_order_release);
     }
   } else if (tid == 0) {
     const unsigned long long t0 = globaltimer_ns();
     unsigned spins = 0;
-    int ok = 1;
-    while (aref(gb->gen).load(cuda::memory_order_acquire) == s_gen) {
-      if (*(volatile int*)&gb->error) { ok = 0; break; }
+    while (aref(gb->count).load(cuda::memory_order_acquire) < target) {
+      if (*(volatile int*)&gb->error) { s_ok = 0; break; }
       if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > ctl.limit_ns) {
         atomicExch(&gb->error, 1);
-        ok = 0;
+        s_ok = 0;
         break;
       }
     }
-    s_dec = ok ? *(volatile int*)&gb->decision : -1;
   }
   __syncthreads();
-  return s_dec;
+  return s_ok ? 0 : -1;
+}
+
+// Wait for the scalars of phase ph - 1 (gen >= ph). Returns the decision
+// (1: every problem has stopped), or -1 on timeout. Uniform over the block.
+__device__ int lsqr_wait_release(const LsqrCtl& ctl, int ph) {
+  __shared__ int s_res;
+  if (ph == 0) return 0;
+  using aref = cuda::atomic_ref<unsigned, cuda::thread_scope_device>;
+  GridBarrier* gb = ctl.gb;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const unsigned long long t0 = globaltimer_ns();
+    unsigned spins = 0;
+    int res = 0;
+    while (aref(gb->gen).load(cuda::memory_order_acquire) < (unsigned)ph) {
+      if (*(volatile int*)&gb->error) { res = -1; break; }
+      if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > ctl.limit_ns) {
+        atomicExch(&gb->error, 1);
+        res = -1;
+        break;
+      }
+    }
+    s_res = res < 0 ? -1 : *(volatile int*)&gb->decision;
+  }
+  __syncthreads();
+  return s_res;
 }
 
 constexpr int LSQR_TCACHE = 4;   // tile descriptors a block keeps in shared memory
@@ -532,11 +574,29 @@ __global__ void __launch_bounds__(256, 2) k_lsqr(const LsqrProb<T, Acc>* __restr
     if (tid == 0) s_pid[k] = p;
   }
   __syncthreads();
-  // phase 0: F(init), B(init); then F_i, B_i for i = 1, 2, ... until every
-  // problem has stopped (decided by the last block at each barrier)
+  // band rows of the cached tiles, forward and transposed (one-term PSFs:
+  // they are the same in every pass of the launch)
+  if (ctl.band_cache) {
+    for (int k = 0; k < LSQR_TCACHE; ++k) {
+      const int tile = blockIdx.x + k * (int)G;
+      if (tile >= ctl.ntiles) break;
+      const LsqrProb<T, Acc>& P = s_prob[k];
+      const int tl = tile - P.tile_begin;
+      const int r0 = (tl % P.nt) * TM, c0 = (tl / P.nt) * TN;
+      Acc* cb = sm + ctl.cache_off + (size_t)k * 4 * TM * ctl.band_pw;
+      load_bands<Acc>(P.op, false, 0, r0, c0, tile_geom(P.op, false), cb, cb + TM * ctl.band_pw);
+      load_bands<Acc>(P.op, true, 0, r0, c0, tile_geom(P.op, true), cb + 2 * TM * ctl.band_pw,
+                      cb + 3 * TM * ctl.band_pw);
+    }
+    __syncthreads();
+  }
+  // phase 0: F(init), B(init); then F_i, B_i for i = 1, 2, ...; phase
+  // ph = 2 i + half. The stop of every problem, decided with the scalars of
+  // phase ph - 1, is read at the first tile of phase ph.
   for (int it = 0;; ++it) {
     for (int half = 0; half < 2; ++half) {
       const bool isF = (half == 0);
+      const int ph = 2 * it + half;
       int k = 0;
       for (int tile = blockIdx.x; tile < ctl.ntiles; tile += G, ++k) {
         const bool cached = k < LSQR_TCACHE;
@@ -546,13 +606,20 @@ __global__ void __launch_bounds__(256, 2) k_lsqr(const LsqrProb<T, Acc>* __restr
         const int r0 = (tl % P.nt) * TM, c0 = (tl / P.nt) * TN;
         Acc red[3];
         __syncthreads();   // shared memory of the previous tile is free
-        const bool did = isF ? lsqr_pass_F<T, Acc>(P, ctl, p, it == 0, it == 1, r0, c0, sm, red)
-                             : lsqr_pass_B<T, Acc>(P, ctl, p, it == 0, r0, c0, sm, red);
-        if (!did) continue;   // uniform over the block
-        tile_partial(red, ctl.part + (size_t)tile * 3, scratch);
+        Acc* cbr = nullptr;
+        Acc* cbc = nullptr;
+        if (cached && ctl.band_cache) {
+          Acc* cb = sm + ctl.cache_off + (size_t)k * 4 * TM * ctl.band_pw + (isF ? 0 : 2 * TM * ctl.band_pw);
+          cbr = cb;
+          cbc = cb + TM * ctl.band_pw;
+        }
+        const int rc = isF ? lsqr_pass_F<T, Acc>(P, ctl, p, it == 0, it == 1, r0, c0, sm, red, cbr, cbc, ph, k == 0)
+                           : lsqr_pass_B<T, Acc>(P, ctl, p, it == 0, r0, c0, sm, red, cbr, cbc, ph, k == 0);
+        if (rc < 0) return;    // every problem has stopped, or a wait timed out (uniform over the block)
+        if (rc == 0) continue;
+        tile_partial(red, phase_part(ctl, ph) + (size_t)tile * 3, scratch);
       }
-      const int dec = lsqr_phase_end<T, Acc>(probs, ctl, coef, isF, it);
-      if (dec != 0) return;
+      if (lsqr_phase_arrive<T, Acc>(probs, ctl, coef, isF, it, ph) < 0) return;
     }
   }
 }

@@ -18,6 +18,11 @@ constexpr int TY = 8;         // blockDim.y; blockDim.x = 32
 constexpr int PIX = TN / TY;  // output pixels per thread
 constexpr int MAX_BAND = 96;  // widest band a tile kernel accepts
 
+// Column (within the tile) of output pixel j of this thread: each thread owns
+// PIX consecutive columns of row threadIdx.x, so the column pass can slide one
+// register window over them.
+__device__ __forceinline__ int pix_col(int j) { return PIX * (int)threadIdx.y + j; }
+
 // One level operator: A = sum_t (Cc_t kron Cr_t), acting as X -> sum_t Cr_t X Cc_t^T.
 // A 1-D factor C (m x m) is stored as B[r][k] = C[r, (r + dlo + k) mod m],
 // k < w ("circular band"). The transposed band has dlo_T = -(dlo + w - 1) and
@@ -186,21 +191,32 @@ __device__ __forceinline__ void conv_term(const TileGeom& g, const Acc* sx, Acc*
     }
   }
   __syncthreads();
-  // step 2: along c with the column factor
+  // step 2: along c with the column factor, for this thread's PIX
+  // consecutive columns (their windows share PIX + w - 1 rows of sz, read
+  // once into registers in the unrolled form)
+  const int cb = pix_col(0);
+  if constexpr (KW > 0) {
+    Acc zv[KW + PIX - 1];
+    const Acc* zs0 = sz + (cb - g.lo + g.dlo) * TM + r;
 #pragma unroll
-  for (int j = 0; j < PIX; ++j) {
-    const int c = threadIdx.y + TY * j;
-    const Acc* bcol = sbc + c * pw;
-    const Acc* zs = sz + (c - g.lo + g.dlo) * TM + r;
-    if constexpr (KW > 0) {
+    for (int q = 0; q < KW + PIX - 1; ++q) zv[q] = (q < w + PIX - 1) ? zs0[q * TM] : Acc(0);
+#pragma unroll
+    for (int j = 0; j < PIX; ++j) {
+      const Acc* bcol = sbc + (cb + j) * pw;
       Acc a0 = 0, a1 = 0;
 #pragma unroll
       for (int k = 0; k < KW; k += 2) {
-        if (k < w) a0 += bcol[k] * zs[k * TM];
-        if (k + 1 < w) a1 += bcol[k + 1] * zs[(k + 1) * TM];
+        if (k < w) a0 += bcol[k] * zv[j + k];
+        if (k + 1 < w) a1 += bcol[k + 1] * zv[j + k + 1];
       }
       out[j] += a0 + a1;
-    } else {
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < PIX; ++j) {
+      const int c = cb + j;
+      const Acc* bcol = sbc + c * pw;
+      const Acc* zs = sz + (c - g.lo + g.dlo) * TM + r;
       Acc acc = 0;
 #pragma unroll 4
       for (int k = 0; k < w; ++k) acc += bcol[k] * zs[k * TM];
@@ -209,7 +225,7 @@ __device__ __forceinline__ void conv_term(const TileGeom& g, const Acc* sx, Acc*
   }
 }
 
-// out[j] += (A or A^T applied to the tile in sx) at pixel (r0+tx, c0+ty+8j).
+// out[j] += (A or A^T applied to the tile in sx) at pixel (r0+tx, c0+pix_col(j)).
 // Caller has loaded sx (and synchronised). Uses sz/sb scratch.
 // `first_loaded`: the caller already loaded term 0's bands (together with the
 // tile, before one barrier).
@@ -254,10 +270,10 @@ __global__ void __launch_bounds__(256) k_blur(BandOp<Acc> op, int tr, const T* _
     const int r = r0 + threadIdx.x;
 #pragma unroll
     for (int j = 0; j < PIX; ++j) {
-      const int c = c0 + threadIdx.y + TY * j;
+      const int c = c0 + pix_col(j);
       if (r < m && c < m) {
         Y[r + (size_t)c * m] = store_cast<T, Acc>(out[j]);
-        if (xcopy) xcopy[r + (size_t)c * m] = store_cast<T, Acc>(sx[(threadIdx.y + TY * j - g.lo) * g.H + threadIdx.x - g.lo]);
+        if (xcopy) xcopy[r + (size_t)c * m] = store_cast<T, Acc>(sx[(pix_col(j) - g.lo) * g.H + threadIdx.x - g.lo]);
       }
     }
   }

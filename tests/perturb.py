@@ -17,7 +17,7 @@ import numpy as np
 from oracle import operators as O
 from oracle import solvers as S
 
-UNIT_ROUNDOFF = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24}
+UNIT_ROUNDOFF = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24, "bf16": 2.0 ** -8}
 
 
 @contextlib.contextmanager

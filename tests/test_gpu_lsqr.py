@@ -85,3 +85,28 @@ def test_lsqr_zero_rhs():
     xo = torch.full((m * m,), 5.0, device="cuda", dtype=torch.float32)
     its = api.lsqr_solve(psf, m, "mm", 1e-3, z, z, torch.zeros(2 * m * m, device="cuda"), None, xo)
     assert its == 0 and float(xo.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_autotuned_shapes_give_identical_results(prec):
+    """The launch-shape autotuner runs every LSQR shape on the first solve of
+    a size class and keeps the fastest; all shapes compute the same result,
+    so a tuned context and an untuned one agree bit for bit."""
+    import torch
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    m = 128
+    A, b, x_true, psf = problem(m)
+    x0 = 0.9 * x_true
+    qx, qy = O.L_apply(x0)
+    a0 = S.mm_surrogate(qx, qy, 0.03)
+    outs = []
+    for tune in (True, False):
+        ctx = api.Context(0)
+        ctx.set_autotune(tune)
+        xo = torch.empty(m * m, device="cuda", dtype=dt)
+        its = api.lsqr_solve(psf, m, "mm", 2e-4, img_to_dev(b, dt), img_to_dev(x0, dt), planes_to_dev(*a0, dt),
+                             None, xo, ctx=ctx)
+        outs.append((its, dev_to_img(xo, m)))
+        ctx.close()
+    assert outs[0][0] == outs[1][0]
+    assert np.array_equal(outs[0][1], outs[1][1])
