@@ -110,10 +110,9 @@ __device__ __forceinline__ void df_sum_loads(const float2* p, int n, float& hi, 
   }
 }
 
-// Kahan-compensated warp dot over strided elements, returned as (hi, lo).
-__device__ __forceinline__ float2 warp_df(float acc, float comp) {
-  // combine acc (with Kahan residue -comp) across the warp
-  float hi = acc, lo = -comp;
+// Warp sum of double-float pairs (hi, lo) with a fixed xor butterfly; every
+// lane ends with the same total.
+__device__ __forceinline__ float2 warp_df_pair(float hi, float lo) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
@@ -122,6 +121,10 @@ __device__ __forceinline__ float2 warp_df(float acc, float comp) {
   }
   return make_float2(hi, lo);
 }
+
+// Kahan-compensated warp dot over strided elements, returned as (hi, lo):
+// acc with Kahan residue -comp, combined across the warp.
+__device__ __forceinline__ float2 warp_df(float acc, float comp) { return warp_df_pair(acc, -comp); }
 
 // Block sum of NV per-thread partials (float or double); the result (double)
 // is valid in thread (0,0) only. `scratch` needs NV * 32 doubles. The warp

@@ -953,6 +953,34 @@ struct Engine {
     CK(cudaGetLastError());
   }
 
+  // the chunk partials of nslot outputs in gpart2 -> their destinations
+  template <class Map> void part_reduce(int nslot, int nch, const float2* part, const Map& map) {
+    if (nslot <= 0) return;
+    count_launch();
+    k_part_reduce<Map><<<(nslot + 7) / 8, 256, 0, st>>>(nslot, nch, part, map);
+  }
+
+  // k_vchunk and its reduction: dots into out[r * ostride] (VCH_DOTS), the
+  // norm into *outnorm (VCH_NORM)
+  void vchunk(size_t n, int nrows, const float* V, const double* coef, int cstride, float* x, int mode, double* out,
+              int ostride, double* outnorm, int nch, int E) {
+    REQUIRE((size_t)(nrows + 1) * nch <= gpart2_cap, "Gram partial buffer too small");
+    count_launch();
+    k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, nrows, V, n, coef, cstride, x, mode, gpart2, E);
+    const int r0 = (mode & VCH_DOTS) ? 0 : nrows;
+    const int r1 = (mode & VCH_NORM) ? nrows + 1 : nrows;
+    part_reduce(r1 - r0, nch, gpart2 + (size_t)r0 * nch, RedRows{r0, nrows, ostride, out, outnorm});
+  }
+
+  // k_gram_col and its reduction into G_A, G_D, g_A, g_D (t == null: D part only)
+  void gram_col(int m, int nr, const float* vj, int jout, const float* V, const float* t, const T* wx, const T* wy,
+                const float* atbf, const float* dtcf, int nch, int E) {
+    REQUIRE((size_t)2 * (nr + 2) * nch <= gpart2_cap, "Gram partial buffer too small");
+    count_launch();
+    k_gram_col<T><<<nch, VCH_THREADS, 0, st>>>(m, nr, vj, jout, V, t, wx, wy, atbf, dtcf, gpart2, E);
+    part_reduce(2 * (nr + 2), nch, gpart2, RedGramCol{nr, jout, gkmax, t != nullptr ? 1 : 0, gGA, gGD, ggA, ggD});
+  }
+
   double gcv_projected_fused(const Level<T>& L, const T* wx, const T* wy, bool has_c, double s, double bnorm2,
                              double atb2, bool kc_hit) {
     const size_t n = L.n;
@@ -963,7 +991,6 @@ struct Engine {
     int E = VCH_E;
     while (E > 1 && (n + (size_t)E * VCH_THREADS - 1) / ((size_t)E * VCH_THREADS) < (size_t)2 * ctx->nsm) E >>= 1;
     const int nch = (int)((n + (size_t)E * VCH_THREADS - 1) / ((size_t)E * VCH_THREADS));
-    unsigned* cnt = d_cnt + 16;
     float* V = reinterpret_cast<float*>(gV);
     float* t = reinterpret_cast<float*>(gt);
     const float* atbf = reinterpret_cast<const float*>(gatb);
@@ -1003,7 +1030,8 @@ struct Engine {
       const size_t smb = (size_t)nb * E * VCH_THREADS * sizeof(float);
       if (smb > 48 * 1024) CK(cudaFuncSetAttribute(k_gram_dcols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
       count_launch();
-      k_gram_dcols<T><<<nch, VCH_THREADS, smb, st>>>(m, j0, nb, V, wx, wy, dtcf, gpart2, cnt, gGD, ld, ggD, E);
+      k_gram_dcols<T><<<nch, VCH_THREADS, smb, st>>>(m, j0, nb, V, wx, wy, dtcf, gpart2, E);
+      part_reduce((j0 + nb + 1) * nb, nch, gpart2, RedDcols{j0, nb, ld, gGD, ggD});
     }
     CK(cudaGetLastError());
     // new columns: v_j = t / ||t|| (written by the A pass), z = A v_j, t = A^T z
@@ -1011,16 +1039,13 @@ struct Engine {
       const int j = C.kc_cols;
       blur_dev(L, false, gt, gz, C.gpend, gV + (size_t)j * n);
       blur_dev(L, true, gz, gt, nullptr, nullptr);
-      { count_launch(); k_gram_col<T><<<nch, VCH_THREADS, 0, st>>>(m, j, V + (size_t)j * n, j, V, t, wx, wy, atbf,
-            dtcf, gpart2, cnt, gGA, gGD, ld, ggA, ggD, E); }
+      gram_col(m, j, V + (size_t)j * n, j, V, t, wx, wy, atbf, dtcf, nch, E);
       ++C.kc_cols;
       if (C.kc_cols < kcap) {
         // next direction: two classical Gram-Schmidt passes (the first reuses
         // the Gram column G_A[i][j] = V_i . t)
-        { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, j + 1, V, n, gGA + j, ld, t,
-              VCH_UPDATE | VCH_DOTS, gpart2, cnt, gh, 1, nullptr, E); }
-        { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, j + 1, V, n, gh, 1, t,
-              VCH_UPDATE | VCH_NORM, gpart2, cnt, nullptr, 0, C.gpend, E); }
+        vchunk(n, j + 1, V, gGA + j, ld, t, VCH_UPDATE | VCH_DOTS, gh, 1, nullptr, nch, E);
+        vchunk(n, j + 1, V, gh, 1, t, VCH_UPDATE | VCH_NORM, nullptr, 0, C.gpend, nch, E);
       }
       CK(cudaGetLastError());
     }
@@ -1040,12 +1065,9 @@ struct Engine {
           // shift direction orth(D^T c) against V_0..V_{kdim-1} (two Gram-Schmidt passes)
           float* vc = reinterpret_cast<float*>(gknext);
           CK(cudaMemcpyAsync(vc, gdtc, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
-          { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, kdim, V, n, nullptr, 0, vc, VCH_DOTS, gpart2,
-                cnt, gh, 1, nullptr, E); }
-          { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, kdim, V, n, gh, 1, vc, VCH_UPDATE | VCH_DOTS,
-                gpart2, cnt, gh2, 1, nullptr, E); }
-          { count_launch(); k_vchunk<<<nch, VCH_THREADS, 0, st>>>(n, kdim, V, n, gh2, 1, vc, VCH_UPDATE | VCH_NORM,
-                gpart2, cnt, nullptr, 0, d_box + 22, E); }
+          vchunk(n, kdim, V, nullptr, 0, vc, VCH_DOTS, gh, 1, nullptr, nch, E);
+          vchunk(n, kdim, V, gh, 1, vc, VCH_UPDATE | VCH_DOTS, gh2, 1, nullptr, nch, E);
+          vchunk(n, kdim, V, gh2, 1, vc, VCH_UPDATE | VCH_NORM, nullptr, 0, d_box + 22, nch, E);
           CK(cudaGetLastError());
           double nc2 = 0.0;
           CK(cudaMemcpyAsync(&nc2, d_box + 22, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1054,8 +1076,7 @@ struct Engine {
             float* vres = V + (size_t)kr * n;
             blur_dev(L, false, gknext, gz, d_box + 22, gV + (size_t)kr * n);
             blur_dev(L, true, gz, gy, nullptr, nullptr);
-            { count_launch(); k_gram_col<T><<<nch, VCH_THREADS, 0, st>>>(m, kdim, vres, kr, V,
-                  reinterpret_cast<float*>(gy), wx, wy, atbf, dtcf, gpart2, cnt, gGA, gGD, ld, ggA, ggD, E); }
+            gram_col(m, kdim, vres, kr, V, reinterpret_cast<float*>(gy), wx, wy, atbf, dtcf, nch, E);
             CK(cudaGetLastError());
             kk = kdim + 1;
             kshift = kr;

@@ -143,22 +143,23 @@ __global__ void k_Lt_w(int m, const Acc* __restrict__ qx, const Acc* __restrict_
 // ---- fused Krylov-basis kernels ------------------------------------------------
 // Each block owns one contiguous chunk of the vectors; per-chunk partial sums
 // are kept as double-float pairs (float hi + float lo, error-free TwoSum, see
-// df_add) and the block that finishes last adds the chunks in a fixed order.
+// df_add) in part[slot * nchunks + chunk], and k_part_reduce adds the chunks
+// of every output slot in a fixed order, one warp per slot.
 constexpr int VCH_E = 8;                 // elements per thread per chunk
 constexpr int VCH_THREADS = 256;
 constexpr int VCH_CHUNK = VCH_E * VCH_THREADS;
 enum VchunkMode { VCH_UPDATE = 1, VCH_DOTS = 2, VCH_NORM = 4 };
 
-// x -= sum_{i<nrows} coef[i*cstride] V_i (VCH_UPDATE); then V_i . x for
-// i < nrows into out[i*ostride] (VCH_DOTS) and/or x . x into *outnorm
-// (VCH_NORM). Float vectors only (the Krylov basis is held in working
+// x -= sum_{i<nrows} coef[i*cstride] V_i (VCH_UPDATE); then the chunk
+// partials of V_i . x for i < nrows into slots 0..nrows-1 (VCH_DOTS) and/or
+// of x . x into slot nrows (VCH_NORM), summed by k_part_reduce with
+// RedRows. Float vectors only (the Krylov basis is held in working
 // precision); part needs (nrows + 1) * gridDim.x float2.
 __global__ void __launch_bounds__(VCH_THREADS) k_vchunk(size_t n, int nrows, const float* __restrict__ V, size_t ldv,
     const double* __restrict__ coef, int cstride, float* __restrict__ x, int mode, float2* __restrict__ part,
-    unsigned* cnt, double* out, int ostride, double* outnorm, int E) {
+    int E) {
   __shared__ float xs[VCH_CHUNK];
   __shared__ float cs[512];
-  __shared__ int s_last;
   const int nch = gridDim.x, ch = blockIdx.x;
   const int CH = E * VCH_THREADS;
   const size_t beg = (size_t)ch * CH;
@@ -211,23 +212,6 @@ __global__ void __launch_bounds__(VCH_THREADS) k_vchunk(size_t n, int nrows, con
       part[(size_t)nrows * nch + ch] = make_float2(hi, lo);
     }
   }
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    s_last = (atomicAdd(cnt, 1u) == (unsigned)nch - 1);
-    __threadfence();
-  }
-  __syncthreads();
-  if (!s_last) return;
-  const int r0 = (mode & VCH_DOTS) ? 0 : nrows;
-  const int r1 = (mode & VCH_NORM) ? nrows + 1 : nrows;
-  for (int r = r0 + tid; r < r1; r += VCH_THREADS) {
-    float hi = 0.f, lo = 0.f;
-    df_sum_loads(part + (size_t)r * nch, nch, hi, lo);
-    const double v = (double)hi + (double)lo;
-    if (r < nrows) out[(size_t)r * ostride] = v; else *outnorm = v;
-  }
-  if (tid == 0) *cnt = 0;
 }
 
 // One Gram column for the basis vector vj against rows V_0..V_{nr-1} and
@@ -235,16 +219,17 @@ __global__ void __launch_bounds__(VCH_THREADS) k_vchunk(size_t n, int nrows, con
 // (computed here),
 //   GA[i*ld + jout] = V_i . t, GD[i*ld + jout] = V_i . y   (i < nr),
 //   GA[jout*ld + jout] = vj . t, GD[jout*ld + jout] = vj . y,
-//   gA[jout] = atb . vj, gD[jout] = dtc . vj (dtc may be null -> 0).
-// t == null computes only the D part (GD, gD), for a basis whose GA is known.
+//   gA[jout] = atb . vj, gD[jout] = dtc . vj (dtc may be null -> 0),
+// as chunk partials in slots 2i (A part) and 2i+1 (D part) for the rows
+// i = 0..nr (row nr is vj) and i = nr+1 (the g entries), summed by
+// k_part_reduce with RedGramCol. t == null computes only the D part (GD, gD),
+// for a basis whose GA is known.
 template <typename T>
 __global__ void __launch_bounds__(VCH_THREADS) k_gram_col(int m, int nr, const float* __restrict__ vj, int jout,
     const float* __restrict__ V, const float* __restrict__ t, const T* __restrict__ wx, const T* __restrict__ wy,
-    const float* __restrict__ atb, const float* __restrict__ dtc, float2* __restrict__ part, unsigned* cnt,
-    double* GA, double* GD, int ld, double* gA, double* gD, int E) {
+    const float* __restrict__ atb, const float* __restrict__ dtc, float2* __restrict__ part, int E) {
   __shared__ float ts[VCH_CHUNK];
   __shared__ float ys[VCH_CHUNK];
-  __shared__ int s_last;
   const size_t n = (size_t)m * m;
   const int nch = gridDim.x, ch = blockIdx.x;
   const int CH = E * VCH_THREADS;
@@ -288,43 +273,21 @@ __global__ void __launch_bounds__(VCH_THREADS) k_gram_col(int m, int nr, const f
       part[(size_t)(2 * i + 1) * nch + ch] = r2;
     }
   }
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    s_last = (atomicAdd(cnt, 1u) == (unsigned)nch - 1);
-    __threadfence();
-  }
-  __syncthreads();
-  if (!s_last) return;
-  for (int sidx = tid; sidx < 2 * (nrows + 1); sidx += VCH_THREADS) {
-    const int i = sidx >> 1;
-    const bool a_part = (sidx & 1) == 0;
-    if (a_part && !with_a) continue;
-    float hi = 0.f, lo = 0.f;
-    df_sum_loads(part + (size_t)sidx * nch, nch, hi, lo);
-    const double v = (double)hi + (double)lo;
-    if (i < nrows) {
-      const int row = i < nr ? i : jout;
-      if (a_part) GA[(size_t)row * ld + jout] = v; else GD[(size_t)row * ld + jout] = v;
-    } else {
-      if (a_part) gA[jout] = v; else gD[jout] = v;
-    }
-  }
-  if (tid == 0) *cnt = 0;
 }
 
 // D part of nb Gram columns at once (the basis is cached, so G_A is known):
 // for the columns j = j0 .. j0+nb-1, with y_j = L^T diag(w^2) L v_j computed
 // here, GD[i*ld + j] = V_i . y_j for i <= j and gD[j] = dtc . v_j (dtc may be
-// null -> 0). Each chunk of V is read once for all nb columns. part needs
-// (j0 + nb + 1) * nb * gridDim.x float2.
+// null -> 0), as chunk partials in slot i * nb + (j - j0) (row i = j0 + nb is
+// the g_D row), summed by k_part_reduce with RedDcols. Each chunk of V is
+// read once for all nb columns. part needs (j0 + nb + 1) * nb * gridDim.x
+// float2.
 constexpr int GDB_NB = 8;
 template <typename T>
 __global__ void __launch_bounds__(VCH_THREADS) k_gram_dcols(int m, int j0, int nb, const float* __restrict__ V,
     const T* __restrict__ wx, const T* __restrict__ wy, const float* __restrict__ dtc, float2* __restrict__ part,
-    unsigned* cnt, double* GD, int ld, double* gD, int E) {
+    int E) {
   extern __shared__ __align__(16) float ysm[];          // [nb][E * VCH_THREADS]
-  __shared__ int s_last;
   const size_t n = (size_t)m * m;
   const int nch = gridDim.x, ch = blockIdx.x;
   const int CH = E * VCH_THREADS;
@@ -377,25 +340,76 @@ __global__ void __launch_bounds__(VCH_THREADS) k_gram_dcols(int m, int j0, int n
       if (lane == 0) part[((size_t)i * nb + c) * nch + ch] = r;
     }
   }
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    s_last = (atomicAdd(cnt, 1u) == (unsigned)nch - 1);
-    __threadfence();
-  }
-  __syncthreads();
-  if (!s_last) return;
-  for (int sidx = tid; sidx < (j1 + 1) * nb; sidx += VCH_THREADS) {
-    const int i = sidx / nb, c = sidx - (sidx / nb) * nb;
-    const int j = j0 + c;
-    if (i < j1 && i > j) continue;      // lower triangle: not stored
-    float hi = 0.f, lo = 0.f;
-    df_sum_loads(part + (size_t)sidx * nch, nch, hi, lo);
-    const double v = (double)hi + (double)lo;
-    if (i < j1) GD[(size_t)i * ld + j] = v; else gD[j] = v;
-  }
-  if (tid == 0) *cnt = 0;
 }
+
+// ---- chunk-partial reduction -----------------------------------------------
+// Output slot s of a chunk kernel is the sum of part[s * nch + c] over the
+// chunks c; one warp per slot, lane l adding chunks l, l + 32, ... (batches of
+// RED_BATCH loads) and the warp butterfly combining the lanes, so the result
+// depends only on the partials and nch. Map::dst(s) gives the destination of
+// slot s (null: not stored).
+constexpr int RED_BATCH = 8;
+template <class Map>
+__global__ void __launch_bounds__(256) k_part_reduce(int nslot, int nch, const float2* __restrict__ part, Map map) {
+  const int lane = threadIdx.x & 31;
+  const int s = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (s >= nslot) return;
+  double* d = map.dst(s);
+  if (d == nullptr) return;
+  const float2* p = part + (size_t)s * nch;
+  float hi = 0.f, lo = 0.f;
+  for (int c0 = 0; c0 < nch; c0 += 32 * RED_BATCH) {
+    float2 q[RED_BATCH];
+#pragma unroll
+    for (int k = 0; k < RED_BATCH; ++k) {
+      const int c = c0 + k * 32 + lane;
+      q[k] = c < nch ? p[c] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < RED_BATCH; ++k) df_add(hi, lo, q[k].x, q[k].y);
+  }
+  const float2 r = warp_df_pair(hi, lo);
+  if (lane == 0) *d = (double)r.x + (double)r.y;
+}
+
+// k_vchunk slots r0 .. : row r < nrows -> out[r * ostride], r == nrows -> *outnorm
+struct RedRows {
+  int r0, nrows, ostride;
+  double* out;
+  double* outnorm;
+  __device__ double* dst(int s) const {
+    const int r = r0 + s;
+    return r < nrows ? out + (size_t)r * ostride : outnorm;
+  }
+};
+
+// k_gram_col slots (see there)
+struct RedGramCol {
+  int nr, jout, ld, with_a;
+  double *GA, *GD, *gA, *gD;
+  __device__ double* dst(int s) const {
+    const int i = s >> 1;
+    const bool a_part = (s & 1) == 0;
+    if (a_part && !with_a) return nullptr;
+    if (i <= nr) {
+      const int row = i < nr ? i : jout;
+      return (a_part ? GA : GD) + (size_t)row * ld + jout;
+    }
+    return (a_part ? gA : gD) + jout;
+  }
+};
+
+// k_gram_dcols slots (see there); the lower triangle is not stored
+struct RedDcols {
+  int j0, nb, ld;
+  double *GD, *gD;
+  __device__ double* dst(int s) const {
+    const int i = s / nb, j = j0 + (s - i * nb);
+    const int j1 = j0 + nb;
+    if (i < j1) return i > j ? nullptr : GD + (size_t)i * ld + j;
+    return gD + j;
+  }
+};
 
 // ---- exact mode: dense matrices of the pair (n <= a few hundred) ------------
 // A[(r + c m), (r' + c' m)] = sum_t Cr_t[r, r'] Cc_t[c, c'], C[r, s] = B[r][(s - r - dlo) mod m].
