@@ -659,9 +659,12 @@ __device__ __forceinline__ double exp2_neg_exponent(double x) {
 // leaves the pivots unchanged. The elimination and its subtractions are those
 // of a Thomas sweep. Warp 0 runs the recurrences while warps 1.. sum the
 // symbol trace (projected mode); all threads call it. wk: 3 kk doubles.
-__device__ double sel_eval(const GcvSelectArgs& a, int kk, const double* dg, const double* eo, const double* f,
-                           double r02, const double* lam, double gamma, double* u, double* wk, double* sh,
-                           double* tr_out) {
+// The single-block selector (exact mode on the tiny levels, and the fallback
+// when no cluster fits) uses this one-directional form; the cluster selector
+// uses the twisted form below.
+__device__ double sel_eval_seq(const GcvSelectArgs& a, int kk, const double* dg, const double* eo, const double* f,
+                               double r02, const double* lam, double gamma, double* u, double* wk, double* sh,
+                               double* tr_out) {
   double* Dv = wk;            // D_i, then alpha_i = f_i / pivot_i
   double* Dp = wk + kk;       // D_{i-1} (same scaling), then beta_i = a_i / pivot_i
   double* cw = wk + 2 * kk;   // a_{i+1} / pivot_i
@@ -760,18 +763,192 @@ __device__ double sel_eval(const GcvSelectArgs& a, int kk, const double* dg, con
   return gamma * gamma * q[0] + r02;
 }
 
-// Symbol trace sum_i 1 / (1 + gamma s rho_i) for one gamma (all threads;
-// loads in batches of 8 per thread, Kahan-compensated float sums).
-__device__ double sel_trace_one(const GcvSelectArgs& a, double gamma, double* sh) {
+// Numerator gamma^2 u^T T u + r0^2 with ((1 - gamma) T + gamma I) u = f
+// (b_i the diagonal, a_i the entry coupling rows i-1 and i), by a twisted
+// elimination at the middle row m: rows 0..m-1 are eliminated downwards
+// (LDL^T pivots through the leading minors D_i = b_i D_{i-1} - a_i^2 D_{i-2},
+// pivot D_i / D_{i-1}) while rows K-1..m+1 are eliminated upwards (UDU^T
+// pivots through the trailing minors E_i = b_i E_{i+1} - a_{i+1}^2 E_{i+2}),
+// row m is solved from both, and the back substitution runs outwards. The
+// matrix is SPD for gamma > 0, so both sets of pivots are positive. The two
+// halves are sequential recurrences run by two threads in different warps
+// (separate FP64 pipes; a single thread issuing FP64 costs ~64 cycles per
+// instruction here, whatever the dependencies); everything else (the
+// coefficients, the reciprocals of the pivots, u^T T u) is parallel.
+// (D_i, D_{i-1}) and (E_i, E_{i+1}) are rescaled together by a power of two
+// every 4 rows, which leaves the pivots unchanged. Warps 2.. sum the symbol
+// trace over the pixels [pix0, pix1) meanwhile (projected mode); all
+// threads call it (at least 96). wk: 3 kk doubles.
+__device__ double sel_eval_tw(const GcvSelectArgs& a, int kk, const double* dg, const double* eo, const double* f,
+                              double r02, double gamma, double* u, double* wk, double* sh, double* tr_out, int pix0,
+                              int pix1) {
+  double* X0 = wk;            // b_i; minor D_i / E_i; 1 / pivot_i
+  double* X1 = wk + kk;       // a^2 of the recurrence; previous minor; multiplier l_i (i < m) / r_i (i > m)
+  double* X2 = wk + 2 * kk;   // eliminated right-hand side; then its product with 1 / pivot_i
+  const double g1 = 1.0 - gamma, g0 = gamma;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int m = kk >> 1;
+  __shared__ double s_trp[32];
+  __shared__ double s_tw[2];
+  // (0) coefficients
+  for (int i = tid; i < kk; i += blockDim.x) {
+    X0[i] = fma(g1, dg[i], g0);
+    double c = 0.0;
+    if (i < m && i > 0) c = g1 * eo[i - 1];
+    else if (i > m && i + 1 < kk) c = g1 * eo[i];
+    X1[i] = c * c;
+  }
+  __syncthreads();
+  // (1) leading minors (thread 0) || trailing minors (thread 32) || trace partial sums (warps 2..)
+  if (tid == 0) {
+    double dm1 = 1.0, dm2 = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double di = fma(-X1[i], dm2, X0[i] * dm1);
+      X0[i] = di;
+      X1[i] = dm1;
+      dm2 = dm1;
+      dm1 = di;
+      if ((i & 3) == 3 && di != 0.0) {
+        const double sc = exp2_neg_exponent(di);
+        dm1 *= sc;
+        dm2 *= sc;
+      }
+    }
+  } else if (tid == 32) {
+    double em1 = 1.0, em2 = 0.0;
+    for (int i = kk - 1, c = 0; i > m; --i, ++c) {
+      const double ei = fma(-X1[i], em2, X0[i] * em1);
+      X0[i] = ei;
+      X1[i] = em1;
+      em2 = em1;
+      em1 = ei;
+      if ((c & 3) == 3 && ei != 0.0) {
+        const double sc = exp2_neg_exponent(ei);
+        em1 *= sc;
+        em2 *= sc;
+      }
+    }
+  } else if (wid >= 2) {
+    const float gs = (float)(gamma * a.s);
+    float sum = 0.f, comp = 0.f;
+    constexpr int B = 8;
+    const int nt = blockDim.x - 64;
+    for (int base = pix0 + tid - 64; base < pix1; base += nt * B) {
+      float r[B];
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        const int i = base + q * nt;
+        r[q] = i < pix1 ? __ldg(a.rho + i) : -1.f;
+      }
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        if (r[q] < 0.f) continue;
+        const float term = __frcp_rn(1.0f + gs * r[q]);
+        const float y = term - comp;
+        const float t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+      }
+    }
+    double trp = warp_sum((double)sum - (double)comp);
+    if (lane == 0) s_trp[wid] = trp;
+  }
+  __syncthreads();
+  // (2) reciprocals of the pivots and the multipliers, in parallel
+  for (int i = tid; i < kk; i += blockDim.x) {
+    if (i == m) continue;
+    const double d = X0[i];
+    const double inv = d != 0.0 ? X1[i] * rcp_d(d) : 0.0;
+    X0[i] = inv;
+    X1[i] = (i < m ? g1 * eo[i] : g1 * eo[i - 1]) * inv;
+  }
+  __syncthreads();
+  // (3) eliminated right-hand sides, downwards (thread 0) and upwards
+  //     (thread 32); trace total (warp 2)
+  if (tid == 0) {
+    if (m > 0) {
+      double y = f[0];
+      X2[0] = y;
+      for (int i = 1; i < m; ++i) {
+        y = fma(-X1[i - 1], y, f[i]);
+        X2[i] = y;
+      }
+      s_tw[0] = X1[m - 1] * y;
+    } else {
+      s_tw[0] = 0.0;
+    }
+  } else if (tid == 32) {
+    if (m + 1 < kk) {
+      double z = f[kk - 1];
+      X2[kk - 1] = z;
+      for (int i = kk - 2; i > m; --i) {
+        z = fma(-X1[i + 1], z, f[i]);
+        X2[i] = z;
+      }
+      s_tw[1] = X1[m + 1] * z;
+    } else {
+      s_tw[1] = 0.0;
+    }
+  } else if (wid == 2) {
+    const int nw = blockDim.x >> 5;
+    double t = (lane >= 2 && lane < nw) ? s_trp[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) *tr_out = t;
+  }
+  __syncthreads();
+  // (3b) the twisted row m; the other rows' eliminated right-hand sides
+  //      times 1 / pivot
+  for (int i = tid; i < kk; i += blockDim.x) {
+    if (i != m) {
+      X2[i] *= X0[i];
+    } else {
+      double gm = X0[m];
+      if (m > 0) gm -= (g1 * eo[m - 1]) * X1[m - 1];
+      if (m + 1 < kk) gm -= (g1 * eo[m]) * X1[m + 1];
+      u[m] = (f[m] - s_tw[0] - s_tw[1]) * rcp_d(gm);
+    }
+  }
+  __syncthreads();
+  // (3c) back substitution outwards from row m
+  if (tid == 0) {
+    double un = u[m];
+    for (int i = m - 1; i >= 0; --i) {
+      un = fma(-X1[i], un, X2[i]);
+      u[i] = un;
+    }
+  } else if (tid == 32) {
+    double un = u[m];
+    for (int i = m + 1; i < kk; ++i) {
+      un = fma(-X1[i], un, X2[i]);
+      u[i] = un;
+    }
+  }
+  __syncthreads();
+  // (4) u^T T u
+  double q[1] = {0.0};
+  for (int i = tid; i < kk; i += blockDim.x) {
+    double tu = dg[i] * u[i];
+    if (i > 0) tu += eo[i - 1] * u[i - 1];
+    if (i + 1 < kk) tu += eo[i] * u[i + 1];
+    q[0] += u[i] * tu;
+  }
+  sel_sumN<1>(q, kk, sh);
+  return gamma * gamma * q[0] + r02;
+}
+
+// Symbol trace sum_i 1 / (1 + gamma s rho_i) over the pixels [pix0, pix1)
+// for one gamma (all threads; loads in batches of 8 per thread,
+// Kahan-compensated float sums).
+__device__ double sel_trace_one(const GcvSelectArgs& a, double gamma, double* sh, int pix0, int pix1) {
   const float gs = (float)(gamma * a.s);
   float sum = 0.f, comp = 0.f;
   constexpr int B = 8;
-  for (int base = threadIdx.x; base < a.npix; base += blockDim.x * B) {
+  for (int base = pix0 + threadIdx.x; base < pix1; base += blockDim.x * B) {
     float r[B];
 #pragma unroll
     for (int q = 0; q < B; ++q) {
       const int i = base + q * blockDim.x;
-      r[q] = i < a.npix ? __ldg(a.rho + i) : -1.f;
+      r[q] = i < pix1 ? __ldg(a.rho + i) : -1.f;
     }
 #pragma unroll
     for (int q = 0; q < B; ++q) {
@@ -786,9 +963,10 @@ __device__ double sel_trace_one(const GcvSelectArgs& a, double gamma, double* sh
   return sel_block_sum((double)sum - (double)comp, sh);
 }
 
-// Trace term for a set of gammas (all threads); returns per-gamma traces in tr[].
+// Trace term for a set of gammas (all threads); returns per-gamma traces in
+// tr[] (projected mode: over the pixels [pix0, pix1)).
 __device__ void sel_traces(const GcvSelectArgs& a, const double* lam, int ng, const double* gam, double* tr,
-                           double* sh) {
+                           double* sh, int pix0, int pix1) {
   for (int g = 0; g < ng; ++g) {
     if (a.exact) {
       double part = 0.0;
@@ -799,7 +977,7 @@ __device__ void sel_traces(const GcvSelectArgs& a, const double* lam, int ng, co
       const double t = sel_block_sum(part, sh);
       if (threadIdx.x == 0) tr[g] = t;
     } else {
-      const double t = sel_trace_one(a, gam[g], sh);
+      const double t = sel_trace_one(a, gam[g], sh, pix0, pix1);
       if (threadIdx.x == 0) tr[g] = t;
     }
   }
@@ -1130,7 +1308,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_gcv_select(GcvSelectArgs a0, Gc
       for (int j = tid; j < npts; j += nth) s_tr[j] = a.trace_tab[j];
       __syncthreads();
     } else {
-      sel_traces(a, lam, npts, s_gam, s_tr, sh);
+      sel_traces(a, lam, npts, s_gam, s_tr, sh, 0, a.npix);
     }
     for (int j = tid; j < npts; j += nth) {
       const double num = sel_numerator(kk, dg, eo, fvec, r02, s_gam[j], scratch + (size_t)j * 2 * kk,
@@ -1152,7 +1330,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_gcv_select(GcvSelectArgs a0, Gc
   // S is free once T is extracted: scratch of the trial-gamma solves
   auto feval = [&](double t) -> double {
     const double gam = pow(10.0, t);
-    const double num = sel_eval(a, kk, dg, eo, fvec, r02, lam, gam, u, S, sh, &s_bc[2]);
+    const double num = sel_eval_seq(a, kk, dg, eo, fvec, r02, lam, gam, u, S, sh, &s_bc[2]);
     const double den = a.n - s_bc[2];
     __syncthreads();
     return num / (den * den);
@@ -1221,12 +1399,14 @@ __global__ void __launch_bounds__(SEL_THREADS) k_gcv_select(GcvSelectArgs a0, Gc
 //    columns (right-looking over the rows of R, its local copy), X passing
 //    through global memory between the two; column q of C is row q, so each
 //    CTA ends with its own rows of C (full rows).
-//  * Householder: per step, the column below the diagonal is gathered from
-//    the row owners and the product C u is summed from per-CTA partials (in
-//    CTA order); every CTA then forms the same u, w, K and updates its rows.
-//  * T's diagonals and p_A, p_D are gathered; the rest (w0, grid, Brent)
-//    runs in CTA 0 alone, the others having left once no remote access
-//    remains.
+//  * Householder: one exchange per step carries the per-CTA partials of
+//    C u (summed in CTA order) and row k+1 from its owner; every CTA then
+//    forms the same w, K, the next column (row k+1 after the update, by
+//    symmetry) and the next reflector, and updates its own rows.
+//  * T's diagonals are gathered; w0 and the Brent control flow run in every
+//    CTA on the same values, while the symbol traces (split by pixel range)
+//    and the grid numerators (split by point) are computed once and
+//    exchanged. Each Brent evaluation uses the twisted elimination.
 // Every value that more than one CTA computes is computed from the same data
 // in the same order, so the copies agree bit for bit.
 constexpr int SCL_NC = 8;
@@ -1235,7 +1415,7 @@ constexpr int SCL_MAXK = 164;
 
 struct SclLayout {
   int K, nrl, ncl;
-  size_t rp, mr, xc, vec, cb, pb, sc, total;   // offsets in doubles
+  size_t rp, mr, xc, vec, cb, pb, total;   // offsets in doubles
 };
 __host__ __device__ inline SclLayout scl_layout(int K) {
   SclLayout L;
@@ -1248,8 +1428,7 @@ __host__ __device__ inline SclLayout scl_layout(int K) {
   L.vec = L.xc + (size_t)K * L.ncl;
   L.cb = L.vec + (size_t)12 * K;
   L.pb = L.cb + (size_t)2 * K;
-  L.sc = L.pb + (size_t)SCL_NC * K;
-  L.total = L.sc + (size_t)2 * SCL_NC * 4;
+  L.total = L.pb + (size_t)2 * SCL_NC * K;
   return L;
 }
 __host__ __device__ inline size_t rp_at(int i, int j) { return (size_t)i * (i + 1) / 2 + j; }
@@ -1269,6 +1448,35 @@ __device__ void scl_forward(int K, int nc, const double* Rp, const double* rdiag
     }
     __syncthreads();
   }
+}
+
+// Householder step arithmetic with explicit roundings, so that every CTA
+// that evaluates an entry gets the same bits: w_j = 2 p_j - 2 K u_j and the
+// rank-2 update m - (u_i w_j + w_i u_j).
+__device__ __forceinline__ double hh_w(double m2K, double uj, double pj) { return __fma_rn(m2K, uj, 2.0 * pj); }
+__device__ __forceinline__ double hh_upd(double m, double ui, double wj, double wi, double uj) {
+  return __dsub_rn(m, __fma_rn(ui, wj, __dmul_rn(wi, uj)));
+}
+
+// Reflector of the column x (len entries) by one warp: alpha = -sign(x_0)
+// ||x||, u = (x - alpha e_0) / sqrt(2 ||x|| (||x|| + |x_0|)), so that
+// (I - 2 u u^T) x = alpha e_0; a column already reduced gives u = 0 and
+// alpha = x_0 (the step leaves the matrix as it is).
+__device__ void scl_reflector_warp(int len, const double* x, double* u, double* alpha_out) {
+  const int lane = threadIdx.x & 31;
+  double acc = 0.0;
+  for (int j = lane; j < len; j += 32) acc += x[j] * x[j];
+  const double nx2 = warp_sum(acc);
+  const double x0 = x[0];
+  const bool reduced = nx2 - x0 * x0 <= 1e-300 * (1.0 + nx2);
+  double alpha = x0, inv_nu = 0.0;
+  if (!reduced) {
+    const double nrm = nx2 * rsqrt_d(nx2);
+    alpha = x0 >= 0 ? -nrm : nrm;
+    inv_nu = rsqrt_d(2.0 * nrm * (nrm + fabs(x0)));
+  }
+  for (int j = lane; j < len; j += 32) u[j] = reduced ? 0.0 : (x[j] - (j == 0 ? alpha : 0.0)) * inv_nu;
+  if (lane == 0) *alpha_out = alpha;
 }
 
 __global__ void __launch_bounds__(SCL_THREADS) k_gcv_select_cl(GcvSelectArgs a0, GcvSelectArgs a1, GcvSelectArgs a2) {
@@ -1301,8 +1509,7 @@ __global__ void __launch_bounds__(SCL_THREADS) k_gcv_select_cl(GcvSelectArgs a0,
   double* colc = rdiag + K;
   double* wk3 = colc + K;         // 3 K, scratch of the trial-gamma solves
   double* cbuf = sdyn + Ly.cb;    // 2 K, double-buffered column exchange
-  double* pbuf = sdyn + Ly.pb;    // SCL_NC x K partial products
-  double* scbuf = sdyn + Ly.sc;   // 2 x SCL_NC x 4 partial scalars (double-buffered)
+  double* pbuf = sdyn + Ly.pb;    // 2 x SCL_NC x K partial products (double-buffered)
   double* Xg = a.work;            // K x K, X through global memory
   double* vg = Xg + (size_t)K * K;            // p_A, p_D through global memory (2 K)
   double* scratch = vg + 2 * (size_t)K;       // grid Thomas scratch, 2 K per point
@@ -1398,83 +1605,91 @@ __global__ void __launch_bounds__(SCL_THREADS) k_gcv_select_cl(GcvSelectArgs a0,
     Mr[(size_t)lq * K + i] = Xc[(size_t)i * ncc + lq];
   }
   __syncthreads();
-  // 5. Householder tridiagonalisation on the distributed rows
+  // 5. Householder tridiagonalisation on the distributed rows. Column k of
+  //    the current matrix is its row k (symmetry): the owner of row k+1
+  //    broadcasts that row with the partial products, and every CTA applies
+  //    the step's rank-2 update to it, which gives column k+1 and the next
+  //    reflector without a second exchange.
+  double* uc = u;          // reflector of the current step
+  double* un = fvec;       // reflector of the next step
+  double* xn = colc;       // next column, below the diagonal
+  double* wv = wk3;        // w of the current step
+  __shared__ double s_hh[2];   // alpha of the current / next step (by parity)
+  __shared__ double s_red[3];  // K, da, dd
+  if (rank == 0)
+    for (int j = tid; j < K - 1; j += nth)
+      for (int r = 0; r < SCL_NC; ++r) cl.map_shared_rank(cbuf, r)[j] = Mr[1 + j];
+  cl.sync();
+  if (wid == 0) scl_reflector_warp(K - 1, cbuf, uc, &s_hh[0]);
+  __syncthreads();
   for (int k = 0; k + 2 < K; ++k) {
     const int len = K - k - 1;
-    double* xb = cbuf + (size_t)(k & 1) * K;
-    double* scb = scbuf + (size_t)(k & 1) * SCL_NC * 4;
-    double nx[1] = {0.0};
-    for (int li = tid; li < nrl; li += nth) {
-      const int i = rank + li * SCL_NC;
-      if (i > k && i < K) { const double v = Mr[(size_t)li * K + k]; nx[0] += v * v; }
-    }
-    sel_sumN<1>(nx, nrl, sh);
-    for (int idx = tid; idx < nrl * SCL_NC; idx += nth) {
-      const int li = idx / SCL_NC, r = idx - li * SCL_NC;
-      const int i = rank + li * SCL_NC;
-      if (i > k && i < K) cl.map_shared_rank(xb, r)[i] = Mr[(size_t)li * K + k];
-    }
-    if (tid < SCL_NC) cl.map_shared_rank(scb, tid)[rank * 4] = nx[0];
-    cl.sync();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int r = 0; r < SCL_NC; ++r) t += scb[r * 4];
-      s_bc[0] = t;
-    }
-    __syncthreads();
-    const double nx2 = s_bc[0];
-    const double x0 = xb[k + 1];
-    if (nx2 - x0 * x0 <= 1e-300 * (1.0 + nx2)) continue;   // already reduced: identical in every CTA
-    if (tid == 0) {
-      const double inx = rsqrt_d(nx2);
-      const double nrm = nx2 * inx;
-      const double alpha = x0 >= 0 ? -nrm : nrm;
-      s_bc[1] = alpha;
-      s_bc[2] = rsqrt_d(2.0 * nrm * (nrm + fabs(x0)));
-    }
-    __syncthreads();
-    const double alpha = s_bc[1], inv_nu = s_bc[2];
-    for (int j = tid; j < len; j += nth) u[j] = (xb[k + 1 + j] - (j == 0 ? alpha : 0.0)) * inv_nu;
-    __syncthreads();
-    // partial p_j = sum over own rows i > k of C[i][k+1+j] u_{i-k-1}, sent to every CTA
+    const int par = k & 1;
+    const bool more = k + 3 < K;
+    double* pb = pbuf + (size_t)par * SCL_NC * K;
+    double* rb = cbuf + (size_t)((k + 1) & 1) * K;
+    const double alpha = s_hh[par];
+    const int li0 = (k + 1 - rank > 0) ? (k + 1 - rank + SCL_NC - 1) / SCL_NC : 0;   // first own row > k
+    // partial products over the own rows, sent to every CTA; row k+1 from its owner
     for (int j = tid; j < len; j += nth) {
       double acc = 0.0;
-      for (int li = 0; li < nrl; ++li) {
+      for (int li = li0; li < nrl; ++li) {
         const int i = rank + li * SCL_NC;
-        if (i > k && i < K) acc += Mr[(size_t)li * K + k + 1 + j] * u[i - k - 1];
+        if (i >= K) break;
+        acc += Mr[(size_t)li * K + k + 1 + j] * uc[i - k - 1];
       }
-      for (int r = 0; r < SCL_NC; ++r) cl.map_shared_rank(pbuf, r)[(size_t)rank * K + j] = acc;
+      for (int r = 0; r < SCL_NC; ++r) cl.map_shared_rank(pb, r)[(size_t)rank * K + j] = acc;
+    }
+    if (more && (k + 1) % SCL_NC == rank) {
+      const double* row = Mr + (size_t)((k + 1) / SCL_NC) * K + k + 2;
+      for (int j = tid; j < len - 1; j += nth)
+        for (int r = 0; r < SCL_NC; ++r) cl.map_shared_rank(rb, r)[j] = row[j];
     }
     cl.sync();
     for (int j = tid; j < len; j += nth) {
       double t = 0.0;
-      for (int r = 0; r < SCL_NC; ++r) t += pbuf[(size_t)r * K + j];
+      for (int r = 0; r < SCL_NC; ++r) t += pb[(size_t)r * K + j];
       p[j] = t;
     }
     __syncthreads();
-    double kd[3] = {0.0, 0.0, 0.0};
-    for (int j = tid; j < len; j += nth) {
-      kd[0] += u[j] * p[j];
-      kd[1] += u[j] * pA[k + 1 + j];
-      kd[2] += u[j] * pD[k + 1 + j];
+    // K = u.p, da = u.p_A, dd = u.p_D, one warp each
+    if (wid < 3) {
+      const double* v = wid == 0 ? p : (wid == 1 ? pA + k + 1 : pD + k + 1);
+      double acc = 0.0;
+      for (int j = lane; j < len; j += 32) acc += uc[j] * v[j];
+      acc = warp_sum(acc);
+      if (lane == 0) s_red[wid] = acc;
     }
-    sel_sumN<3>(kd, len, sh);
-    const double Kc = kd[0], da = kd[1], dd = kd[2];
-    for (int j = tid; j < len; j += nth) p[j] = 2.0 * p[j] - 2.0 * Kc * u[j];   // w
     __syncthreads();
-    for (int li = wid; li < nrl; li += nwarp) {
-      const int i = rank + li * SCL_NC;
-      if (i <= k || i >= K) continue;
-      const double ui = u[i - k - 1], wi = p[i - k - 1];
-      double* Mi = Mr + (size_t)li * K + k + 1;
-      for (int j = lane; j < len; j += 32) Mi[j] -= ui * p[j] + wi * u[j];
-    }
+    const double m2K = -2.0 * s_red[0], da = s_red[1], dd = s_red[2];
+    // w = 2 p - 2 K u; the next column = row k+1 after this step's update
+    const double u0 = uc[0], w0 = hh_w(m2K, u0, p[0]);
     for (int j = tid; j < len; j += nth) {
-      pA[k + 1 + j] -= 2.0 * da * u[j];
-      pD[k + 1 + j] -= 2.0 * dd * u[j];
+      const double wj = hh_w(m2K, uc[j], p[j]);
+      wv[j] = wj;
+      if (more && j >= 1) xn[j - 1] = hh_upd(rb[j - 1], u0, wj, w0, uc[j]);
     }
-    if (tid == 0 && (k + 1) % SCL_NC == rank) Mr[(size_t)((k + 1) / SCL_NC) * K + k] = alpha;
     __syncthreads();
+    // the last warp forms the next reflector while the others update the rows
+    const int nupd = more ? nwarp - 1 : nwarp;
+    if (more && wid == nwarp - 1) {
+      scl_reflector_warp(len - 1, xn, un, &s_hh[par ^ 1]);
+    } else {
+      for (int li = li0 + wid; li < nrl; li += nupd) {
+        const int i = rank + li * SCL_NC;
+        if (i >= K) break;
+        const double ui = uc[i - k - 1], wi = wv[i - k - 1];
+        double* Mi = Mr + (size_t)li * K + k + 1;
+        for (int j = lane; j < len; j += 32) Mi[j] = hh_upd(Mi[j], ui, wv[j], wi, uc[j]);
+      }
+      for (int j = tid; j < len; j += nupd * 32) {
+        pA[k + 1 + j] -= 2.0 * da * uc[j];
+        pD[k + 1 + j] -= 2.0 * dd * uc[j];
+      }
+      if (tid == 0 && (k + 1) % SCL_NC == rank) Mr[(size_t)((k + 1) / SCL_NC) * K + k] = alpha;
+    }
+    __syncthreads();
+    double* t = uc; uc = un; un = t;
   }
   // 6. T's diagonals from the row owners
   for (int li = tid; li < nrl; li += nth) {
@@ -1489,8 +1704,16 @@ __global__ void __launch_bounds__(SCL_THREADS) k_gcv_select_cl(GcvSelectArgs a0,
   }
   if (tid == 0) eo[K - 1] = 0.0;
   cl.sync();
-  // no remote access follows: the rest runs in CTA 0 alone
-  if (rank != 0) return;
+  // From here every CTA holds T, p_A, p_D and runs the same control flow on
+  // the same values; the symbol traces are split over the CTAs by pixel
+  // range and the grid points by index, the pieces exchanged through
+  // distributed shared memory (buffers alternate by parity so that one
+  // exchange never overwrites the previous one while it is read).
+  __shared__ double s_trx[2 * SEL_MAXPTS * SCL_NC];   // grid trace partials [parity][point][rank]
+  __shared__ double s_num[2 * SEL_MAXPTS];            // grid numerators [parity][point]
+  __shared__ double s_bx[2 * SCL_NC];                 // Brent trace partials [parity][rank]
+  const int pix0 = (int)((size_t)a.npix * rank / SCL_NC);
+  const int pix1 = (int)((size_t)a.npix * (rank + 1) / SCL_NC);
   // 7. w0 = T^{-1} p_A, f = p_A + p_D - w0, r0^2 (one Thomas sweep)
   if (tid == 0) {
     sel_tri_solve(K, dg, eo, pA, 0.0, p, u, 0.0);
@@ -1503,27 +1726,41 @@ __global__ void __launch_bounds__(SCL_THREADS) k_gcv_select_cl(GcvSelectArgs a0,
   }
   __syncthreads();
   const double r02 = (a.bnorm2 - s_bc[3]) > 0.0 ? (a.bnorm2 - s_bc[3]) : 0.0;
-  // 8. grid search with widening, then Brent (as k_gcv_select, in every CTA)
+  // 8. grid search with widening, then Brent (as k_gcv_select)
   const int npts = a.npts < SEL_MAXPTS ? a.npts : SEL_MAXPTS;
   double lo = a.lo, hi = a.hi;
   int ext = 0, jbest = 0;
   double fbest = 0.0, step = 0.0;
-  double* lam = nullptr;
   for (;;) {
+    const int gp = ext & 1;
     step = (hi - lo) / (npts - 1);
     for (int j = tid; j < npts; j += nth) s_gam[j] = pow(10.0, (j == npts - 1) ? hi : lo + j * step);
     __syncthreads();
-    if (ext == 0 && a.trace_tab) {
-      for (int j = tid; j < npts; j += nth) s_tr[j] = a.trace_tab[j];
-      __syncthreads();
-    } else {
-      sel_traces(a, lam, npts, s_gam, s_tr, sh);
+    const bool tab = (ext == 0 && a.trace_tab);
+    if (!tab) {
+      sel_traces(a, nullptr, npts, s_gam, s_tr, sh, pix0, pix1);
+      for (int idx = tid; idx < npts * SCL_NC; idx += nth) {
+        const int j = idx / SCL_NC, r = idx - j * SCL_NC;
+        cl.map_shared_rank(s_trx, r)[((size_t)gp * SEL_MAXPTS + j) * SCL_NC + rank] = s_tr[j];
+      }
     }
-    for (int j = tid; j < npts; j += nth) {
+    // this CTA's grid points j = rank, rank + SCL_NC, ...
+    for (int j = rank + tid * SCL_NC; j < npts; j += nth * SCL_NC) {
       double* sc2 = scratch + (size_t)j * 2 * K;
       const double num = sel_numerator(K, dg, eo, fvec, r02, s_gam[j], sc2, sc2 + K);
-      const double den = a.n - s_tr[j];
-      s_f[j] = num / (den * den);
+      for (int r = 0; r < SCL_NC; ++r) cl.map_shared_rank(s_num, r)[gp * SEL_MAXPTS + j] = num;
+    }
+    cl.sync();
+    for (int j = tid; j < npts; j += nth) {
+      double tr;
+      if (tab) {
+        tr = a.trace_tab[j];
+      } else {
+        tr = 0.0;
+        for (int r = 0; r < SCL_NC; ++r) tr += s_trx[((size_t)gp * SEL_MAXPTS + j) * SCL_NC + r];
+      }
+      const double den = a.n - tr;
+      s_f[j] = s_num[gp * SEL_MAXPTS + j] / (den * den);
     }
     __syncthreads();
     jbest = 0;
@@ -1536,11 +1773,17 @@ __global__ void __launch_bounds__(SCL_THREADS) k_gcv_select_cl(GcvSelectArgs a0,
     break;
   }
   auto tgrid = [&](int j) { return (j == npts - 1) ? hi : lo + j * step; };
+  int nev = 0;
   auto feval = [&](double t) -> double {
     const double gam = pow(10.0, t);
-    const double num = sel_eval(a, K, dg, eo, fvec, r02, lam, gam, u, wk3, sh, &s_bc[2]);
-    const double den = a.n - s_bc[2];
-    __syncthreads();
+    const double num = sel_eval_tw(a, K, dg, eo, fvec, r02, gam, u, wk3, sh, &s_bc[2], pix0, pix1);
+    const int bp = nev & 1;
+    ++nev;
+    if (tid < SCL_NC) cl.map_shared_rank(s_bx, tid)[bp * SCL_NC + rank] = s_bc[2];
+    cl.sync();
+    double tr = 0.0;
+    for (int r = 0; r < SCL_NC; ++r) tr += s_bx[bp * SCL_NC + r];
+    const double den = a.n - tr;
     return num / (den * den);
   };
   double A = tgrid(jbest > 0 ? jbest - 1 : 0);
@@ -1585,7 +1828,7 @@ __global__ void __launch_bounds__(SCL_THREADS) k_gcv_select_cl(GcvSelectArgs a0,
     }
   }
   const double tbest = (fx <= fbest) ? x : tgrid(jbest);
-  if (tid == 0) {
+  if (tid == 0 && rank == 0) {
     a.out[0] = pow(10.0, tbest);
     a.out[1] = (double)ext;
     a.out[2] = (fx <= fbest) ? fx : fbest;
