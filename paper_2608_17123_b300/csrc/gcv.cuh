@@ -533,9 +533,10 @@ constexpr int SEL_NVEC = 10;      // k-vectors in shared memory
 
 __host__ __device__ inline int sel_lds(int kk) { return kk | 1; }
 // Global work of one selection: (matrix if not in shared memory), X, C, and
-// the per-grid-point Thomas scratch.
+// the per-grid-point scratch (2 kk per point for the single-block selector,
+// 4 kk for the cluster selector, whose X takes kk^2 + 2 kk).
 inline size_t sel_work_doubles(int kk) {
-  return (kk <= SEL_SMEM_K ? 0 : (size_t)kk * sel_lds(kk)) + (size_t)2 * kk * kk + (size_t)2 * SEL_MAXPTS * kk;
+  return (kk <= SEL_SMEM_K ? 0 : (size_t)kk * sel_lds(kk)) + (size_t)2 * kk * kk + (size_t)4 * SEL_MAXPTS * kk;
 }
 // Dynamic shared memory of k_gcv_select: the k-vectors, then (k <= SEL_SMEM_K)
 // the working matrix.
@@ -934,6 +935,105 @@ __device__ double sel_eval_tw(const GcvSelectArgs& a, int kk, const double* dg, 
   }
   sel_sumN<1>(q, kk, sh);
   return gamma * gamma * q[0] + r02;
+}
+
+// Numerator gamma^2 u^T T u + r0^2 for one gamma by one warp (the grid
+// points of the cluster selector): the twisted elimination of sel_eval_tw,
+// its two recurrences in lanes 0 and 1, which run them as one instruction
+// stream (an FP64 warp instruction costs the same for one lane or two), and
+// its parallel phases over the lanes. X: 4 kk doubles of scratch (global);
+// the whole warp calls it; the result is in every lane.
+__device__ double sel_numerator_warp(int kk, const double* dg, const double* eo, const double* f, double r02,
+                                     double gamma, double* X) {
+  double* X0 = X;
+  double* X1 = X + kk;
+  double* X2 = X + 2 * kk;
+  double* u = X + 3 * kk;
+  const double g1 = 1.0 - gamma, g0 = gamma;
+  const int lane = threadIdx.x & 31;
+  const int m = kk >> 1;
+  const bool fwd = lane == 0;
+  for (int i = lane; i < kk; i += 32) {
+    X0[i] = fma(g1, dg[i], g0);
+    double c = 0.0;
+    if (i < m && i > 0) c = g1 * eo[i - 1];
+    else if (i > m && i + 1 < kk) c = g1 * eo[i];
+    X1[i] = c * c;
+  }
+  __syncwarp();
+  // minors: leading (lane 0, rows 0..m-1), trailing (lane 1, rows kk-1..m+1)
+  if (lane < 2) {
+    const int ns = fwd ? m : kk - 1 - m;
+    double p1 = 1.0, p2 = 0.0;
+    for (int st = 0; st < ns; ++st) {
+      const int i = fwd ? st : kk - 1 - st;
+      const double di = fma(-X1[i], p2, X0[i] * p1);
+      X0[i] = di;
+      X1[i] = p1;
+      p2 = p1;
+      p1 = di;
+      if ((st & 3) == 3 && di != 0.0) {
+        const double sc = exp2_neg_exponent(di);
+        p1 *= sc;
+        p2 *= sc;
+      }
+    }
+  }
+  __syncwarp();
+  for (int i = lane; i < kk; i += 32) {
+    if (i == m) continue;
+    const double d = X0[i];
+    const double inv = d != 0.0 ? X1[i] * rcp_d(d) : 0.0;
+    X0[i] = inv;
+    X1[i] = (i < m ? g1 * eo[i] : g1 * eo[i - 1]) * inv;
+  }
+  __syncwarp();
+  // eliminated right-hand sides: downwards (lane 0), upwards (lane 1)
+  double tw = 0.0;
+  if (lane < 2 && (fwd ? m > 0 : m + 1 < kk)) {
+    const int ns = fwd ? m - 1 : kk - 2 - m;
+    double y = fwd ? f[0] : f[kk - 1];
+    X2[fwd ? 0 : kk - 1] = y;
+    for (int st = 0; st < ns; ++st) {
+      const int i = fwd ? 1 + st : kk - 2 - st;
+      y = fma(-X1[fwd ? i - 1 : i + 1], y, f[i]);
+      X2[i] = y;
+    }
+    tw = X1[fwd ? m - 1 : m + 1] * y;
+  }
+  const double tw0 = __shfl_sync(0xffffffffu, tw, 0), tw1 = __shfl_sync(0xffffffffu, tw, 1);
+  __syncwarp();
+  for (int i = lane; i < kk; i += 32) {
+    if (i != m) {
+      X2[i] *= X0[i];
+    } else {
+      double gm = X0[m];
+      if (m > 0) gm -= (g1 * eo[m - 1]) * X1[m - 1];
+      if (m + 1 < kk) gm -= (g1 * eo[m]) * X1[m + 1];
+      u[m] = (f[m] - tw0 - tw1) * rcp_d(gm);
+    }
+  }
+  __syncwarp();
+  // back substitution outwards: lane 0 rows m-1..0, lane 1 rows m+1..kk-1
+  if (lane < 2) {
+    const int ns = fwd ? m : kk - 1 - m;
+    double un = u[m];
+    for (int st = 0; st < ns; ++st) {
+      const int i = fwd ? m - 1 - st : m + 1 + st;
+      un = fma(-X1[i], un, X2[i]);
+      u[i] = un;
+    }
+  }
+  __syncwarp();
+  double q = 0.0;
+  for (int i = lane; i < kk; i += 32) {
+    double tu = dg[i] * u[i];
+    if (i > 0) tu += eo[i - 1] * u[i - 1];
+    if (i + 1 < kk) tu += eo[i] * u[i + 1];
+    q += u[i] * tu;
+  }
+  q = warp_sum(q);
+  return gamma * gamma * q + r02;
 }
 
 // Symbol trace sum_i 1 / (1 + gamma s rho_i) over the pixels [pix0, pix1)
@@ -1394,7 +1494,9 @@ __global__ void __launch_bounds__(SEL_THREADS) k_gcv_select(GcvSelectArgs a0, Gc
 //  * Cholesky, right-looking: per column, every CTA sends its rows' entries
 //    to all CTAs (distributed shared memory), and every CTA forms the same
 //    column of R and updates its own rows; so every CTA ends with a full
-//    copy of R (packed lower triangle).
+//    copy of R (packed lower triangle). The next column's entries are
+//    updated and sent first, so the barrier completes during the rest of
+//    the update.
 //  * X = R^{-1} [G_A | g_A | g_D] and C = R^{-1} X^T: each CTA solves its own
 //    columns (right-looking over the rows of R, its local copy), X passing
 //    through global memory between the two; column q of C is row q, so each
@@ -1449,6 +1551,13 @@ __device__ void scl_forward(int K, int nc, const double* Rp, const double* rdiag
     __syncthreads();
   }
 }
+
+// Split cluster barrier (every thread of every CTA of the cluster, in
+// arrive / wait alternation): arrive releases this thread's earlier writes,
+// including those to other CTAs' shared memory; wait returns once every
+// thread of the cluster has arrived and acquires their writes.
+__device__ __forceinline__ void scl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void scl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
 
 // Householder step arithmetic with explicit roundings, so that every CTA
 // that evaluates an entry gets the same bits: w_j = 2 p_j - 2 K u_j and the
@@ -1512,7 +1621,7 @@ __global__ void __launch_bounds__(SCL_THREADS) k_gcv_select_cl(GcvSelectArgs a0,
   double* pbuf = sdyn + Ly.pb;    // 2 x SCL_NC x K partial products (double-buffered)
   double* Xg = a.work;            // K x K, X through global memory
   double* vg = Xg + (size_t)K * K;            // p_A, p_D through global memory (2 K)
-  double* scratch = vg + 2 * (size_t)K;       // grid Thomas scratch, 2 K per point
+  double* scratch = vg + 2 * (size_t)K;       // grid scratch, 4 K per point
   auto mapk = [&](int i) { return (a.kshift >= 0 && i == K - 1) ? a.kshift : i; };
   auto GAe = [&](int i, int j) {
     i = mapk(i); j = mapk(j);
@@ -1536,15 +1645,20 @@ __global__ void __launch_bounds__(SCL_THREADS) k_gcv_select_cl(GcvSelectArgs a0,
   __syncthreads();
   const double piv_floor = 1e-14 * s_bc[0];
   cl.sync();   // every CTA of the cluster is running before the first remote store
-  // 2. Cholesky M = R R^T, column by column
+  // 2. Cholesky M = R R^T, column by column. Each column's exchange is a
+  //    split cluster barrier: a CTA updates its entries of the next column
+  //    first, sends them and arrives, then updates the rest of its rows
+  //    while the other CTAs catch up; it waits only before the next pivot.
+  for (int idx = tid; idx < nrl * SCL_NC; idx += nth) {
+    const int li = idx / SCL_NC, r = idx - li * SCL_NC;
+    const int i = rank + li * SCL_NC;
+    if (i < K) cl.map_shared_rank(cbuf, r)[i] = Mr[(size_t)li * K];
+  }
+  scl_arrive();
   for (int c = 0; c < K; ++c) {
     double* cb = cbuf + (size_t)(c & 1) * K;
-    for (int idx = tid; idx < nrl * SCL_NC; idx += nth) {
-      const int li = idx / SCL_NC, r = idx - li * SCL_NC;
-      const int i = rank + li * SCL_NC;
-      if (i >= c && i < K) cl.map_shared_rank(cb, r)[i] = Mr[(size_t)li * K + c];
-    }
-    cl.sync();
+    double* cbn = cbuf + (size_t)((c + 1) & 1) * K;
+    scl_wait();
     if (tid == 0) {
       const double piv = cb[c];
       const double pv = piv > piv_floor ? piv : piv_floor;
@@ -1560,15 +1674,28 @@ __global__ void __launch_bounds__(SCL_THREADS) k_gcv_select_cl(GcvSelectArgs a0,
       colc[i] = v;
     }
     __syncthreads();
+    // own entries of column c+1, updated and sent
+    if (c + 1 < K) {
+      const double cn = colc[c + 1];
+      for (int li = tid; li < nrl; li += nth) {
+        const int i = rank + li * SCL_NC;
+        if (i <= c || i >= K) continue;
+        const double v = Mr[(size_t)li * K + c + 1] - colc[i] * cn;
+        Mr[(size_t)li * K + c + 1] = v;
+        for (int r = 0; r < SCL_NC; ++r) cl.map_shared_rank(cbn, r)[i] = v;
+      }
+    }
+    scl_arrive();
     for (int li = wid; li < nrl; li += nwarp) {
       const int i = rank + li * SCL_NC;
-      if (i <= c || i >= K) continue;
+      if (i <= c + 1 || i >= K) continue;
       const double ci = colc[i];
       double* Mi = Mr + (size_t)li * K;
-      for (int j = c + 1 + lane; j <= i; j += 32) Mi[j] -= ci * colc[j];
+      for (int j = c + 2 + lane; j <= i; j += 32) Mi[j] -= ci * colc[j];
     }
     __syncthreads();
   }
+  scl_wait();
   // 3. X = R^{-1} [G_A | g_A | g_D], own columns q = rank + lq * SCL_NC
   for (int idx = tid; idx < K * ncl; idx += nth) {
     const int i = idx / ncl, lq = idx - (idx / ncl) * ncl;
@@ -1744,11 +1871,11 @@ __global__ void __launch_bounds__(SCL_THREADS) k_gcv_select_cl(GcvSelectArgs a0,
         cl.map_shared_rank(s_trx, r)[((size_t)gp * SEL_MAXPTS + j) * SCL_NC + rank] = s_tr[j];
       }
     }
-    // this CTA's grid points j = rank, rank + SCL_NC, ...
-    for (int j = rank + tid * SCL_NC; j < npts; j += nth * SCL_NC) {
-      double* sc2 = scratch + (size_t)j * 2 * K;
-      const double num = sel_numerator(K, dg, eo, fvec, r02, s_gam[j], sc2, sc2 + K);
-      for (int r = 0; r < SCL_NC; ++r) cl.map_shared_rank(s_num, r)[gp * SEL_MAXPTS + j] = num;
+    // this CTA's grid points j = rank, rank + SCL_NC, ..., one warp each
+    for (int j = rank + wid * SCL_NC; j < npts; j += nwarp * SCL_NC) {
+      double* sc4 = scratch + (size_t)j * 4 * K;
+      const double num = sel_numerator_warp(K, dg, eo, fvec, r02, s_gam[j], sc4);
+      if (lane < SCL_NC) cl.map_shared_rank(s_num, lane)[gp * SEL_MAXPTS + j] = num;
     }
     cl.sync();
     for (int j = tid; j < npts; j += nth) {
