@@ -44,6 +44,13 @@ L2_FLUSH_BYTES = 256 << 20
 # (11 words); pass B reads u_A, u_Lx, u_Ly, v and writes v (5 words); IRLS
 # also reads the two weight planes in both passes (+4 words).
 BYTES_PER_PIX_ITER = {"other": 16 * 4, "irls": 20 * 4}
+# Measured DRAM bytes per k_lsqr launch on this workload: one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, cold cache) of the timed
+# solve's first 80 LSQR launches, on the 128 x 128 and 256 x 256 levels. A
+# launch reads its level's vectors once from HBM (19-25 B per pixel) and
+# iterates from L2. To be retaken whenever k_lsqr changes.
+LSQR_DRAM_BYTES_PER_LAUNCH = 716470
+LSQR_DRAM_SCOPE = "ncu, cold cache, mean over the timed solve's first 80 k_lsqr launches (128x128 and 256x256 levels)"
 
 
 def workload_desc():
@@ -253,7 +260,9 @@ def run_ours(args, rank, world):
     launches = max(1, stats["lsqr_launches"])
     achieved = (bytes_alg / launches) / ((stats["lsqr_ms"] / launches) / 1e3) / 1e9 if stats["lsqr_ms"] > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": LSQR_DRAM_BYTES_PER_LAUNCH,
+                "traffic_scope": LSQR_DRAM_SCOPE,
+                "algorithmic_bytes_per_launch": round(bytes_alg / launches),
                 "kernel": "k_lsqr (persistent cooperative LSQR)", "peak_kind": peak_kind,
                 "lsqr_share_of_step": round(stats["lsqr_ms"] / t_total_ms, 4) if t_total_ms else None}
 
