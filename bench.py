@@ -2,20 +2,27 @@
 """Throughput of the wavelet multilevel l1-deblurring V-cycle on one B300.
 
 Workload (one "step" = one complete V-cycle solve, Alg. 4, of one image):
-m = 512 synthetic piecewise-constant phantoms (40 rectangles, 20 disks,
-intensities U[0,1]), Gaussian PSF sigma = 3 on 15 x 15, 1 % and 5 % noise,
-3-level cycles; step s runs combination s mod 12 of {IRLS, MM, SB} x
-{Haar, Db4} x {X, D} on image seed s mod 4 with noise 1 % (even blocks of 12
-steps) or 5 % (odd blocks). FP32 storage, FP64 reductions.
+the m = 512 workload -- a 512 x 512 synthetic piecewise-constant phantom
+(40 rectangles, 20 disks, intensities U[0,1], seed 0), Gaussian PSF
+sigma = 3 on 15 x 15, b = A x_true + noise at 1 % (even blocks of 12 steps)
+or 5 % (odd blocks), rounded to float32; 3-level cycles; step s runs
+combination s mod 12 of {IRLS, MM, SB} x {Haar, Db4} x {X, D}. FP32 storage;
+the LSQR and Krylov sums are compensated float pairs (double-float) turned
+into double, the scalar recurrences, GCV selection and stopping tests are
+FP64.
 
 Metric: deblurred Mpixel/s (whole job, all ranks). Inputs are resident in
 HBM when the timed region starts; L2 is flushed (256 MB write) before every
-step, outside the CUDA-event pair that times it. `e2e` repeats steps through
-the host-buffer C-ABI call (pinned host input, host->device and
-device->host copies inside the timed region).
+step, outside the CUDA-event pair that times it. `e2e` repeats the same
+steps through the host-buffer C-ABI call (pinned host input, host->device
+and device->host copies inside the timed region). `oracle_parity` compares
+every timed step with the FP64 oracle's stored result of the same case
+(tests/golden/m512_oracle). `large` times a few solves of the large-image
+workload: m = 2048, Gaussian sigma = 6 on 31 x 31 and the 21-pixel motion
+blur at 30 degrees, BF16 storage, 5-level Db4 cycles.
 
-`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
-workload (see cpu_baseline_sample()).
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the
+same workload (see oracle_sample()).
 """
 from __future__ import annotations
 
@@ -38,33 +45,51 @@ SIGMA, PSF_SIZE = 3.0, 15
 LEVELS = 3
 COMBOS = [(s, w, t) for s in ("irls", "mm", "sb") for w in ("haar", "db4") for t in ("X", "D")]
 NOISES = (0.01, 0.05)
+SEED = 0
+GOLDEN = os.path.join(ROOT, "tests", "golden", "m512_oracle")
 L2_FLUSH_BYTES = 256 << 20
-# LSQR algorithmic traffic per pixel per iteration, FP32 storage (4-byte words):
-# pass F reads v, u_A, u_Lx, u_Ly, w, delta and writes u_A, u_Lx, u_Ly, w, delta
-# (11 words); pass B reads u_A, u_Lx, u_Ly, v and writes v (5 words); IRLS
-# also reads the two weight planes in both passes (+4 words).
-BYTES_PER_PIX_ITER = {"other": 16 * 4, "irls": 20 * 4}
-# Measured DRAM bytes per k_lsqr launch on this workload: one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, cold cache) of the timed
-# solve's first 80 LSQR launches, on the 128 x 128 and 256 x 256 levels. A
-# launch reads its level's vectors once from HBM (19-25 B per pixel) and
-# iterates from L2. To be retaken whenever k_lsqr changes.
-LSQR_DRAM_BYTES_PER_LAUNCH = 716470
-LSQR_DRAM_SCOPE = "ncu, cold cache, mean over the timed solve's first 80 k_lsqr launches (128x128 and 256x256 levels)"
+
+# Large-image workload (m = 2048, 5-level Db4, BF16 storage): steps cycle
+# through these (PSF, solver, transfer) cases.
+LARGE_M = 2048
+LARGE_CASES = [("gauss31", "mm", "X"), ("motion21", "irls", "D"), ("gauss31", "sb", "D"),
+               ("motion21", "mm", "X"), ("gauss31", "irls", "X"), ("motion21", "sb", "D")]
+
+
+def lsqr_bytes_per_pixel_iter(elem, x_elem, irls):
+    """Algorithmic LSQR traffic per pixel per iteration: pass F reads v,
+    u_A, u_Lx, u_Ly, w and delta and writes u_A, u_Lx, u_Ly, w, delta; pass B
+    reads u_A, u_Lx, u_Ly, v and writes v -- 14 storage words and 2 words of
+    the iterate type (delta); IRLS also reads the two weight planes in both
+    passes (+4 storage words)."""
+    return 14 * elem + 2 * x_elem + (4 * elem if irls else 0)
+
+
+# DRAM bytes per k_lsqr launch from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum), to be retaken whenever k_lsqr changes; the scope
+# says which launch was captured.
+LSQR_DRAM = {
+    "m512": (None, "not captured for the current kernel"),
+    "large": (None, "not captured for the current kernel"),
+}
 
 
 def workload_desc():
     return {"workload": "m512_gauss_s3_15x15_3level_12combos", "m": M, "psf": f"gaussian sigma={SIGMA} {PSF_SIZE}x{PSF_SIZE}",
-            "levels": LEVELS, "combos": "irls/mm/sb x haar/db4 x X/D", "noise": "1%,5%",
-            "phantom": "40 rect + 20 disk", "precision": "fp32 storage, fp64 reductions",
+            "levels": LEVELS, "combos": "irls/mm/sb x haar/db4 x X/D", "noise": "1%,5%", "seed": SEED,
+            "phantom": "40 rect + 20 disk", "precision": "fp32 storage, double-float (compensated fp32) sums, "
+            "fp64 scalar recurrences / GCV / stopping tests",
             "l2": "flushed (256 MB write) before every step"}
 
 
 def step_spec(s):
     solver, wavelet, transfer = COMBOS[s % len(COMBOS)]
     noise = NOISES[(s // len(COMBOS)) % 2]
-    seed = s % 4
-    return solver, wavelet, transfer, noise, seed
+    return solver, wavelet, transfer, noise
+
+
+def case_name(solver, wavelet, transfer, noise):
+    return f"{solver}-{wavelet}-{transfer}-{noise:g}"
 
 
 def load_peaks():
@@ -74,6 +99,14 @@ def load_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6400.0, "fallback"
+
+
+def load_golden():
+    p = os.path.join(GOLDEN, "index.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        return json.load(f)
 
 
 # ------------------------------------------------------------------ clocks
@@ -124,18 +157,16 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ inputs
-def make_inputs(api, torch, s, psf_dev):
-    """Phantom, PSF and noise from the input generator; b_true = A x_true by
-    the library's own forward blur (level 0, FP64)."""
+def make_b(api, torch, m, x_true, psf, noise, noise_seed):
+    """b = A x_true + noise, with A x_true by the library's own level-0 blur
+    (FP64), rounded to float32 (the values the FP32 path stores)."""
     from paper_2608_17123_b300 import inputs as I
-    solver, wavelet, transfer, noise, seed = step_spec(s)
-    x_true = I.phantom(M, 40, 20, seed)
     xd = torch.from_numpy(I.to_colmajor(x_true).ravel()).cuda()
     bd = torch.empty_like(xd)
-    api.apply_blur(I.gaussian_psf(SIGMA, PSF_SIZE), M, xd, bd)
-    b_true = I.from_colmajor(bd.cpu().numpy(), M)
-    b = I.add_noise(b_true, I.noise_direction(M, 10_000 + seed), noise)
-    return b, x_true
+    api.apply_blur(psf, m, xd, bd)
+    b_true = I.from_colmajor(bd.cpu().numpy(), m)
+    b = I.add_noise(b_true, I.noise_direction(m, noise_seed), noise)
+    return b.astype(np.float32).astype(np.float64)
 
 
 # ------------------------------------------------------------------ sharding
@@ -159,6 +190,39 @@ def max_over_ranks(t_ms, world):
     return float(t.item())
 
 
+# ------------------------------------------------------------------ parity
+def parity_summary(results, golden):
+    """Every timed step against the FP64 oracle's stored result of its case:
+    x on the stored pixel sample (relative 2-norm), outer iterations and
+    gamma per level."""
+    if golden is None:
+        return {"available": False, "why": "tests/golden/m512_oracle/index.json missing"}
+    idx = np.load(os.path.join(GOLDEN, "sample_index.npy"))
+    rows = []
+    for (name, x_colmajor, iters, mu) in results:
+        c = golden["cases"].get(name)
+        if c is None:
+            continue
+        xo = np.load(os.path.join(GOLDEN, name + ".npz"))["x_samples"].astype(np.float64)
+        xs = x_colmajor[idx]
+        dx = float(np.linalg.norm(xs - xo) / np.linalg.norm(xo))
+        dit = max(abs(a - b) for a, b in zip(iters, c["iters"]))
+        dmu = max(abs(a - b) / b for a, b in zip(mu, c["mu"]))
+        rows.append((name, dx, dit, dmu, c["spread_x"], max(c["spread_mu"])))
+    if not rows:
+        return {"available": False, "why": "no timed step has a stored oracle case"}
+    return {"available": True, "reference": "FP64 oracle, tests/golden/m512_oracle (16384-pixel sample)",
+            "steps_compared": len(rows),
+            "max_rel_diff_x": max(r[1] for r in rows),
+            "median_rel_diff_x": float(np.median([r[1] for r in rows])),
+            "x_within_1e-4": sum(r[1] <= 1e-4 for r in rows),
+            "iters_within_1": sum(r[2] <= 1 for r in rows),
+            "mu_within_1pct": sum(r[3] <= 1e-2 for r in rows),
+            "max_rel_diff_mu": max(r[3] for r in rows),
+            "max_oracle_spread_x": max(r[4] for r in rows),
+            "worst": sorted(rows, key=lambda r: -r[1])[0][0]}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world):
     import torch
@@ -173,24 +237,24 @@ def run_ours(args, rank, world):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     total = args.warmup + args.steps
     steps = shard_steps(rank, args.warmup, args.steps)
+    x_true = I.phantom(M, 40, 20, SEED)
+    bs = {nz: make_b(api, torch, M, x_true, psf, nz, 10_000 + SEED) for nz in NOISES}
     # inputs resident in HBM before timing
-    dev_inputs = []
-    host_inputs = []
+    dev_inputs, host_inputs = [], []
     for s in steps:
-        b, _ = make_inputs(api, torch, s, psf_dev)
-        bb = torch.from_numpy(I.to_colmajor(b).ravel()).cuda()
-        dev_inputs.append(bb)
+        b = bs[step_spec(s)[3]]
+        dev_inputs.append(torch.from_numpy(I.to_colmajor(b).ravel()).cuda())
         host_inputs.append(I.to_colmajor(b).ravel())
-    x_dev = torch.empty(M * M, dtype=torch.float64, device="cuda")
-    per_level_counts = []
+    x_out = [torch.empty(M * M, dtype=torch.float64, device="cuda") for _ in range(args.steps)]
+    x_warm = torch.empty(M * M, dtype=torch.float64, device="cuda")
 
-    def solve_dev(i):
-        solver, wavelet, transfer, _, _ = step_spec(steps[i])
-        return api.deblur_solve_device(dev_inputs[i], psf_dev, M, PSF_SIZE, x_dev, solver, wavelet, LEVELS, transfer,
+    def solve_dev(i, xd):
+        solver, wavelet, transfer, _ = step_spec(steps[i])
+        return api.deblur_solve_device(dev_inputs[i], psf_dev, M, PSF_SIZE, xd, solver, wavelet, LEVELS, transfer,
                                        precision="fp32", ctx=ctx, stream=stream.cuda_stream)
 
     for i in range(args.warmup):
-        solve_dev(i)
+        solve_dev(i, x_warm)
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
@@ -199,19 +263,19 @@ def run_ours(args, rank, world):
     ctx.reset_stats()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    times = []
-    for i in range(args.warmup, total):
+    times, results = [], []
+    for k, i in enumerate(range(args.warmup, total)):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         torch.cuda.nvtx.range_push("timed")     # lets a profiler select exactly the timed steps
-        r = solve_dev(i)
+        r = solve_dev(i, x_out[k])
         torch.cuda.nvtx.range_pop()
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
-        per_level_counts.append((step_spec(steps[i])[0], r["iters"], r["inner"]))
+        results.append((steps[i], r))
     torch.cuda.synchronize()
     clk = clocks.stop()
     stats = ctx.stats()
@@ -222,9 +286,16 @@ def run_ours(args, rank, world):
     pixels = M * M * args.steps * world
     value = pixels / (t_total_ms / 1e3) / 1e6
 
-    # e2e through the host-buffer call (pinned input; copies inside the timed region)
-    # --e2e-steps 0 skips this pass (profiling runs only; the line then has no e2e number)
-    e2e_steps = max(0, min(args.steps, args.e2e_steps))
+    # the reconstructions of the timed steps against the FP64 oracle
+    par_in = []
+    for k, (s, r) in enumerate(results):
+        solver, wavelet, transfer, noise = step_spec(s)
+        par_in.append((case_name(solver, wavelet, transfer, noise), x_out[k].cpu().numpy(), r["iters"], r["mu"]))
+    parity = parity_summary(par_in, load_golden())
+
+    # e2e: the same steps through the host-buffer call (pinned input; copies
+    # inside the timed region); --e2e-steps 0 skips it (profiling runs only)
+    e2e_steps = args.steps if args.e2e_steps < 0 else min(args.steps, args.e2e_steps)
     pinned_b = [torch.from_numpy(host_inputs[args.warmup + i]).pin_memory() for i in range(e2e_steps)]
     psf_host = torch.from_numpy(I.to_colmajor(psf).ravel()).pin_memory()
     x_host = torch.empty(M * M, dtype=torch.float64).pin_memory()
@@ -232,7 +303,7 @@ def run_ours(args, rank, world):
     from paper_2608_17123_b300 import _lib as L
     e2e_ms = 0.0
     for i in range(e2e_steps):
-        solver, wavelet, transfer, _, _ = step_spec(steps[args.warmup + i])
+        solver, wavelet, transfer, _ = step_spec(steps[args.warmup + i])
         o, g = api.make_opts("fp32")
         mu = np.zeros(LEVELS)
         it = np.zeros(LEVELS, dtype=np.int32)
@@ -247,30 +318,18 @@ def run_ours(args, rank, world):
         e2e_ms += (time.perf_counter() - t0) * 1e3
     e2e_value = M * M * e2e_steps * world / (e2e_ms / 1e3) / 1e6 if e2e_steps else None
 
-    # batched and served forms on the same timed images (host buffers, like e2e)
-    forms = {}
-    if world == 1 and args.forms:
-        forms = run_forms(api, ctx, torch, [host_inputs[args.warmup + i] for i in range(args.steps)],
-                          [steps[args.warmup + i] for i in range(args.steps)], psf)
-
-    # roofline of the dominant kernel (LSQR persistent kernel)
+    # roofline of k_lsqr on this workload (finest-level launches)
     peak, peak_kind = load_peaks()
-    bytes_alg = (stats["lsqr_pixel_iters_irls"] * BYTES_PER_PIX_ITER["irls"]
-                 + stats["lsqr_pixel_iters_other"] * BYTES_PER_PIX_ITER["other"])
-    launches = max(1, stats["lsqr_launches"])
-    achieved = (bytes_alg / launches) / ((stats["lsqr_ms"] / launches) / 1e3) / 1e9 if stats["lsqr_ms"] > 0 else 0.0
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": LSQR_DRAM_BYTES_PER_LAUNCH,
-                "traffic_scope": LSQR_DRAM_SCOPE,
-                "algorithmic_bytes_per_launch": round(bytes_alg / launches),
-                "kernel": "k_lsqr (persistent cooperative LSQR)", "peak_kind": peak_kind,
-                "lsqr_share_of_step": round(stats["lsqr_ms"] / t_total_ms, 4) if t_total_ms else None}
+    roofline = lsqr_roofline(stats, 4, 4, peak, peak_kind, t_total_ms, "m512",
+                             note="the level's LSQR vectors (~20 MB) stay in the 126 MB L2: latency- and "
+                                  "barrier-bound, not HBM-bound, at this size")
 
     line = {
         "metric": "deblurred Mpixel/s", "value": round(value, 4), "unit": "Mpixel/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_total_ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic phantoms (inputs module), b = A x_true by the library's blur + seeded noise",
+        "data": "synthetic phantoms (inputs module), b = A x_true by the library's blur + seeded noise, "
+                "rounded to float32",
         "config": workload_desc(),
         "images_per_s": round(args.steps * world / (t_total_ms / 1e3), 4),
         "e2e": None if e2e_value is None else
@@ -278,14 +337,91 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": M * M * 8 + PSF_SIZE * PSF_SIZE * 8, "d2h_bytes_per_step": M * M * 8 + LEVELS * 12},
         "gpu_launches": int(stats["kernel_launches"]),
         "roofline": roofline,
+        "oracle_parity": parity,
         "clocks": clk,
         "counts": {"lsqr_launches": int(stats["lsqr_launches"]), "gcv_calls": int(stats["gcv_calls"]),
                    "outer_iterations": int(stats["outer_iterations"])},
         "step_split": {"lsqr_ms_per_step": round(stats["lsqr_ms"] / args.steps, 2),
                        "gcv_ms_per_step": round(stats.get("gcv_ms", 0.0) / args.steps, 2)},
     }
-    line.update(forms)
-    return line, per_level_counts, times
+    if world == 1 and args.large_steps > 0:
+        line["large"] = run_large(api, torch, ctx, args.large_steps, flush, peak, peak_kind)
+    if world == 1 and args.forms:
+        line.update(run_forms(api, ctx, torch, [host_inputs[args.warmup + i] for i in range(args.steps)],
+                              [steps[args.warmup + i] for i in range(args.steps)], psf))
+    return line, results
+
+
+def lsqr_roofline(stats, elem, x_elem, peak, peak_kind, t_total_ms, key, note):
+    """achieved = algorithmic bytes of the finest-level k_lsqr launches /
+    their CUDA-event time (the library records an event pair around every
+    LSQR launch on the solve's stream when profiling is on)."""
+    bytes_alg = (stats["lsqr_fine_pixel_iters_irls"] * lsqr_bytes_per_pixel_iter(elem, x_elem, True)
+                 + stats["lsqr_fine_pixel_iters_other"] * lsqr_bytes_per_pixel_iter(elem, x_elem, False))
+    launches = max(1, stats["lsqr_fine_launches"])
+    ms = stats["lsqr_fine_ms"]
+    achieved = (bytes_alg / launches) / ((ms / launches) / 1e3) / 1e9 if ms > 0 else 0.0
+    traffic, scope = LSQR_DRAM[key]
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic, "traffic_scope": scope,
+            "algorithmic_bytes_per_launch": round(bytes_alg / launches),
+            "kernel": "k_lsqr (persistent cooperative LSQR), finest-level launches",
+            "launches": int(stats["lsqr_fine_launches"]), "peak_kind": peak_kind,
+            "lsqr_share_of_step": round(stats["lsqr_ms"] / t_total_ms, 4) if t_total_ms else None,
+            "note": note}
+
+
+def run_large(api, torch, ctx, nsteps, flush, peak, peak_kind):
+    """A few timed solves of the large-image workload: m = 2048, Gaussian
+    sigma = 6 on 31 x 31 or the 21-pixel motion blur at 30 degrees, 1 %
+    noise, BF16 storage, 5-level Db4 cycles; with the finest-level k_lsqr
+    roofline."""
+    from paper_2608_17123_b300 import inputs as I
+    m = LARGE_M
+    R = int(round(40 * math.sqrt(m / 512)))
+    x_true = I.phantom(m, R, R // 2, SEED)
+    psfs = {"gauss31": I.gaussian_psf(6.0, 31), "motion21": I.motion_psf(21.0, 30.0, 21)}
+    bdev, pdev = {}, {}
+    for name, p in psfs.items():
+        b = make_b(api, torch, m, x_true, p, 0.01, 10_000 + SEED)
+        bdev[name] = torch.from_numpy(I.to_colmajor(b).ravel()).cuda()
+        pdev[name] = torch.from_numpy(I.to_colmajor(p).ravel()).cuda()
+    xd = torch.empty(m * m, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def solve(k):
+        pname, solver, transfer = LARGE_CASES[k % len(LARGE_CASES)]
+        return api.deblur_solve_device(bdev[pname], pdev[pname], m, psfs[pname].shape[0], xd, solver, "db4", 5,
+                                       transfer, precision="bf16", ctx=ctx, stream=stream.cuda_stream)
+
+    solve(0)                                   # warm-up (first launches of the size class)
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    times, rres, cases = [], [], []
+    for k in range(nsteps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = solve(k)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        x = I.from_colmajor(xd.cpu().numpy(), m)
+        rres.append(float(np.linalg.norm(x - x_true) / np.linalg.norm(x_true)))
+        cases.append({"case": "-".join(LARGE_CASES[k % len(LARGE_CASES)]), "ms": round(times[-1], 1),
+                      "iters": r["iters"], "rre_vs_phantom": round(rres[-1], 4)})
+    stats = ctx.stats()
+    t = sum(times)
+    return {"workload": f"m{m}_db4_5level_bf16", "m": m, "steps": nsteps, "ms_per_step": round(t / nsteps, 1),
+            "value": round(m * m * nsteps / (t / 1e3) / 1e6, 4), "unit": "Mpixel/s",
+            "precision": "bf16 storage (image, planes, Krylov vectors), fp32 iterate and LSQR correction",
+            "cases": cases,
+            "roofline": lsqr_roofline(stats, 2, 4, peak, peak_kind, t, "large",
+                                      note="BF16 LSQR vectors of a 2048 x 2048 level: ~80-90 MB, near the "
+                                           "L2 size"),
+            "step_split": {"lsqr_ms_per_step": round(stats["lsqr_ms"] / nsteps, 1),
+                           "gcv_ms_per_step": round(stats.get("gcv_ms", 0.0) / nsteps, 1)}}
 
 
 def run_forms(api, ctx, torch, bs, step_ids, psf):
@@ -322,8 +458,6 @@ def run_forms(api, ctx, torch, bs, step_ids, psf):
     def rel(a, b):
         return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
-    # Poisson arrivals at 80 % of the batched throughput, each image twice:
-    # latency from submit to completion as the server reports it
     rng = np.random.default_rng(2026)
     rate = 0.8 * len(imgs) / t_batch
     order = [i % len(imgs) for i in range(2 * len(imgs))]
@@ -358,7 +492,9 @@ def run_forms(api, ctx, torch, bs, step_ids, psf):
 
 # ------------------------------------------------------------------ oracle sample
 def gcv_calls(solver, level, outer):
-    """GCV estimates a level makes (the schedule of Sec. 3 as implemented)."""
+    """GCV estimates a level makes under the schedule of Sec. 3 (3-level
+    cycles): IRLS re-estimates at every outer iteration, except on the fine
+    level, where it estimates at k = 0 and k = 3; MM and SB at k = 0, 1, 2."""
     if solver == "irls":
         if level == 0 and LEVELS >= 3:
             return 1 + (1 if outer > 3 else 0)
@@ -366,98 +502,175 @@ def gcv_calls(solver, level, outer):
     return min(3, outer)
 
 
-def cpu_baseline_sample(counts, budget_s=20.0):
-    """Time the FP64 oracle on a bounded sample of the workload and scale it
-    to Mpixel/s: per level, oracle LSQR iterations on that level's problem
-    (m = 512, 256, 128; MM form, Db4 hierarchy) and one oracle GCV (projected,
-    k = 40) on the 128 x 128 level, scaled by pixel count to the other levels;
-    the per-solve work (LSQR iterations and GCV calls per level) comes from
-    `counts` (the GPU run's own counts for the same steps) or, without them,
-    from the work model below."""
-    try:
-        from threadpoolctl import threadpool_limits
-        limiter, cores = threadpool_limits(limits=1), 1
-    except ImportError:           # not installed: BLAS keeps its own threads
-        import contextlib
-        limiter, cores = contextlib.nullcontext(), os.cpu_count()
+def sample_unit_costs(levels_to_time, lsqr_iters=(8, 16, 32)):
+    """Seconds per LSQR iteration and per GCV call of the FP64 oracle on the
+    m = 512 workload's own level problems (Db4 hierarchy, 1 % noise): LSQR on
+    the MM form (shift from the Tikhonov-free start), GCV as IRLS calls it
+    (the weighted pair with the weights of the level's restricted data, the
+    k = 40, 80, 160 doubling)."""
     from oracle import operators as O
     from oracle import solvers as S
     from paper_2608_17123_b300 import inputs as I
-    with limiter:
-        g = I.gaussian_factor(SIGMA, PSF_SIZE)
-        A = O.KronOp.from_factors(M, g, g)
-        x_true = I.phantom(M, 40, 20, 0)
-        b = I.add_noise(A.apply(x_true), I.noise_direction(M, 10_000), 0.01)
-        As, bs = [A], [b]
-        for _ in range(LEVELS - 1):
-            As.append(As[-1].coarsen("db4"))
-            bs.append(O.restrict(bs[-1], "db4"))
-        t_iter = []
-        t0_all = time.perf_counter()
-        for lvl in range(LEVELS):
-            mm = As[lvl].m
-            z = (np.zeros((mm - 1, mm)), np.zeros((mm, mm - 1)))
-            sub = S.Subproblem(As[lvl], bs[lvl], c=z)
-            its = 12 if lvl == 0 else 20
-            t = time.perf_counter()
-            _, k = sub.solve(1e-3, np.zeros((mm, mm)), S.opts_with(lsqr_maxit=its, lsqr_atol=0, lsqr_btol=0))
-            t_iter.append((time.perf_counter() - t) / max(k, 1))
-        sub = S.Subproblem(As[-1], bs[-1], c=None)
+    g = I.gaussian_factor(SIGMA, PSF_SIZE)
+    A = O.KronOp.from_factors(M, g, g)
+    x_true = I.phantom(M, 40, 20, SEED)
+    b = I.add_noise(A.apply(x_true), I.noise_direction(M, 10_000 + SEED), 0.01)
+    As, bs = [A], [b]
+    for _ in range(LEVELS - 1):
+        As.append(As[-1].coarsen("db4"))
+        bs.append(O.restrict(bs[-1], "db4"))
+    t_lsqr, t_gcv = {}, {}
+    for lvl in range(LEVELS):
+        mm = As[lvl].m
+        z = (np.zeros((mm - 1, mm)), np.zeros((mm, mm - 1)))
+        sub = S.Subproblem(As[lvl], bs[lvl], c=z)
+        its = lsqr_iters[lvl]
         t = time.perf_counter()
-        sub.gcv(S.opts_with(proj_dim=40, proj_dim_max=40))
-        t_gcv_c = time.perf_counter() - t
-        elapsed = time.perf_counter() - t0_all
-    t_gcv = [t_gcv_c * (4 ** (LEVELS - 1 - l)) for l in range(LEVELS)]
-    tot_t, tot_pix = 0.0, 0
-    for solver, iters, inner in counts:
+        _, k = sub.solve(1e-3, np.zeros((mm, mm)), S.opts_with(lsqr_maxit=its, lsqr_atol=0, lsqr_btol=0))
+        t_lsqr[lvl] = (time.perf_counter() - t) / max(k, 1)
+        if lvl in levels_to_time:
+            w = S.irls_weights(*O.L_apply(bs[lvl] / (2.0 ** lvl)), 0.03)
+            t = time.perf_counter()
+            S.Subproblem(As[lvl], bs[lvl], weights=w).gcv(S.opts_with())
+            t_gcv[lvl] = time.perf_counter() - t
+    return t_lsqr, t_gcv
+
+
+def _unit_costs_worker(q, levels_to_time):
+    q.put(sample_unit_costs(levels_to_time))
+
+
+def unit_costs_with_threads(threads, levels_to_time):
+    """sample_unit_costs in a fresh process whose BLAS uses `threads`
+    threads (the variables must be set before numpy loads)."""
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = str(threads)
+    try:
+        ctx = mp.get_context("spawn")
+        q = ctx.Queue()
+        p = ctx.Process(target=_unit_costs_worker, args=(q, tuple(levels_to_time)))
+        p.start()
+        res = q.get()
+        p.join()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return res
+
+
+def model_solve_seconds(t_lsqr, t_gcv, golden, names):
+    """Oracle seconds per solve of the given cases: the oracle's own recorded
+    work counts (outer iterations and LSQR iterations per level, from its
+    stored runs of these cases) times the measured unit costs."""
+    tot = 0.0
+    for nm in names:
+        c = golden["cases"][nm]
         for l in range(LEVELS):
-            tot_t += inner[l] * t_iter[l] + gcv_calls(solver, l, iters[l]) * t_gcv[l]
-        tot_pix += M * M
-    value = tot_pix / tot_t / 1e6
-    sample = (f"oracle LSQR iterations on the m=512/256/128 levels ({t_iter[0]*1e3:.1f}/{t_iter[1]*1e3:.1f}/"
-              f"{t_iter[2]*1e3:.1f} ms per iteration) and one projected GCV (k=40) on the 128x128 level "
-              f"({t_gcv_c:.2f} s, scaled by pixel count), combined with the per-level LSQR iteration and GCV "
-              f"counts of {len(counts)} solves; {elapsed:.1f} s of CPU work")
-    return {"value": value, "unit": "Mpixel/s", "cores": cores, "kind": "oracle", "sample": sample}
+            tot += c["inner"][l] * t_lsqr[l] + gcv_calls(c["solver"], l, c["iters"][l]) * t_gcv[l]
+    return tot / len(names)
 
 
-# Per-solve work model (LSQR iterations and outer iterations per level, finest
-# first) of the 12 combinations on this workload, from a B300 run of this
-# benchmark; used by the reference arm, which has no GPU run to count from.
-WORK_MODEL = [
-    ("irls", [18, 50, 50], [1366, 3916, 2124]),
-    ("mm", [19, 50, 50], [1343, 2607, 727]),
-    ("sb", [31, 50, 50], [685, 2761, 999]),
-]
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_sample(names):
+    """The cpu_baseline of our line: the oracle's unit costs on this host
+    (1 BLAS thread and all cores), scaled to Mpixel/s with the oracle's
+    recorded work counts of the timed steps' cases."""
+    golden = load_golden()
+    if golden is None:
+        return None
+    names = [n for n in names if n in golden["cases"]]
+    out = {}
+    t0 = time.perf_counter()
+    for threads in (1, os.cpu_count() or 1):
+        tl, tg = unit_costs_with_threads(threads, (0, 1, 2))
+        sec = model_solve_seconds(tl, tg, golden, names)
+        out[threads] = (M * M / sec / 1e6, sec, tl, tg)
+    elapsed = time.perf_counter() - t0
+    nc = os.cpu_count() or 1
+    v_all, sec_all, tl, tg = out[nc]
+    v1, sec1, _, _ = out[1]
+    wall = [golden["cases"][n].get("oracle_wall_s_one_thread") for n in names]
+    return {"value": v_all, "unit": "Mpixel/s", "cores": nc, "kind": "oracle",
+            "cpu": cpu_model(),
+            "one_thread": {"value": v1, "seconds_per_solve": round(sec1, 1)},
+            "seconds_per_solve": round(sec_all, 1),
+            "sample": (f"FP64 oracle on this host: seconds per LSQR iteration on the 512/256/128 levels "
+                       f"({tl[0]*1e3:.1f}/{tl[1]*1e3:.1f}/{tl[2]*1e3:.1f} ms with {nc} BLAS threads) and per "
+                       f"IRLS-type GCV call ({tg[0]:.2f}/{tg[1]:.2f}/{tg[2]:.2f} s), times the oracle's own "
+                       f"recorded counts (outer and LSQR iterations per level) of the {len(names)} timed cases; "
+                       f"{elapsed:.0f} s of CPU work"),
+            "full_solve_reference_s": {"note": "complete single-thread oracle solves of the same cases, timed when "
+                                               "the stored results were written (another host)",
+                                       "median": float(np.median([w for w in wall if w])) if any(wall) else None}}
 
 
 def run_reference(args, rank, world):
+    """The FP64 oracle on the host cores: step s times LSQR iterations on the
+    three level problems and one GCV call on level s mod 3 (a bounded sample
+    of the workload's solves); the Mpixel/s value scales the measured unit
+    costs by the oracle's recorded counts of the workload's cases."""
     if rank != 0:
         return None
-    samples = []
-    for _ in range(args.warmup + args.steps):
-        t = time.perf_counter()
-        cb = cpu_baseline_sample(WORK_MODEL, budget_s=5.0)
-        samples.append((cb, time.perf_counter() - t))
-    timed = samples[args.warmup:]
-    value = statistics.mean(c["value"] for c, _ in timed)
-    cb = dict(timed[-1][0])
-    cb["value"] = value
-    line = {"metric": "deblurred Mpixel/s", "value": value, "unit": "Mpixel/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * M * M / (value * 1e6), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_desc(), "impl": "reference",
-            "cpu_baseline": cb, "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0,
-                                        "d2h_bytes_per_step": 0}}
-    return line
+    golden = load_golden()
+    if golden is None:
+        return {"impl": "reference", "unavailable": "stored oracle counts (tests/golden/m512_oracle) missing"}
+    names = [case_name(*step_spec(s)) for s in range(args.warmup, args.warmup + args.steps)]
+    names = [n for n in names if n in golden["cases"]]
+    for s in range(args.warmup):
+        sample_unit_costs((s % LEVELS,), lsqr_iters=(2, 4, 8))
+    tl_acc = {l: [] for l in range(LEVELS)}
+    tg_acc = {l: [] for l in range(LEVELS)}
+    t_steps = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        tl, tg = sample_unit_costs((s % LEVELS,))
+        t_steps.append(time.perf_counter() - t0)
+        for l in range(LEVELS):
+            tl_acc[l].append(tl[l])
+        for l, v in tg.items():
+            tg_acc[l].append(v)
+    tl = {l: statistics.median(v) for l, v in tl_acc.items()}
+    tg = {l: statistics.median(v) if v else float("nan") for l, v in tg_acc.items()}
+    sec = model_solve_seconds(tl, tg, golden, names)
+    value = M * M / sec / 1e6
+    nc = os.cpu_count() or 1
+    cb = {"value": value, "unit": "Mpixel/s", "cores": nc, "kind": "oracle", "cpu": cpu_model(),
+          "sample": (f"{args.steps} steps, each: LSQR iterations on the 512/256/128 level problems and one GCV "
+                     f"call on one level (the level cycles with the step); unit costs (medians) "
+                     f"{tl[0]*1e3:.1f}/{tl[1]*1e3:.1f}/{tl[2]*1e3:.1f} ms per LSQR iteration, "
+                     f"{tg[0]:.2f}/{tg[1]:.2f}/{tg[2]:.2f} s per GCV call, scaled by the oracle's recorded counts "
+                     f"of the cases -> {sec:.0f} s per solve"),
+          "seconds_per_solve": round(sec, 1)}
+    ms_step = 1e3 * statistics.mean(t_steps)
+    return {"metric": "deblurred Mpixel/s", "value": value, "unit": "Mpixel/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_desc(), "impl": "reference", "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=12)
+    ap.add_argument("--steps", type=int, default=24)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=-1, help="-1: every timed step")
+    ap.add_argument("--large-steps", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", dest="forms", action="store_false",
@@ -475,10 +688,11 @@ def main():
         if line is not None:
             print(json.dumps(line), flush=True)
         return
-    line, counts, _ = run_ours(args, rank, world)
+    line, results = run_ours(args, rank, world)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline_sample(counts)
+            names = [case_name(*step_spec(s)) for s, _ in results]
+            line["cpu_baseline"] = oracle_sample(names)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -82,6 +82,12 @@ typedef struct {
   int    lsqr_maxit;         /* 100                                           */
   int    lsqr_warm_start;    /* 1: LSQR solves for the correction from x^(k)  */
   db_precision precision;    /* storage precision of images and iterates      */
+  int    barrier_timeout_us; /* 2,000,000: limit of every device-side wait of */
+                             /*   the persistent LSQR launch (its grid        */
+                             /*   barriers). A wait that runs out ends the    */
+                             /*   launch on every block and the call returns  */
+                             /*   DB_ETIMEOUT; the context stays usable. 0    */
+                             /*   expires at the first wait (a test setting). */
 } db_opts;
 
 typedef struct db_context db_context;
@@ -178,6 +184,12 @@ db_status db_server_submit(db_server* srv, const db_request* req, uint64_t* tick
  * outputs are written; latency_ms = submit to completion), DB_ETIMEOUT if not
  * yet, or the solve's own error status. A ticket can be polled until done. */
 db_status db_server_poll(db_server* srv, uint64_t ticket, int timeout_us, double* latency_ms);
+/* Withdraw a request. A queued one leaves the queue at once; a resident one
+ * stops at the next scheduler step boundary (its slot and device memory are
+ * released). Its poll then returns DB_ECANCELLED and its outputs are not
+ * written. A request that has already finished is left as it is (DB_OK; its
+ * poll returns its result). DB_EINVAL for an unknown ticket. */
+db_status db_server_cancel(db_server* srv, uint64_t ticket);
 /* Drain the queue, stop the scheduler and free everything. */
 db_status db_server_destroy(db_server* srv);
 
@@ -198,6 +210,12 @@ typedef struct {
   uint64_t gcv_calls;
   uint64_t outer_iterations;
   double   gcv_ms;
+  /* the same LSQR counters restricted to level 0 (the finest level) of
+   * single-image solves */
+  uint64_t lsqr_fine_launches;
+  double   lsqr_fine_ms;
+  double   lsqr_fine_pixel_iters_irls;
+  double   lsqr_fine_pixel_iters_other;
 } db_stats;
 
 db_status db_set_profiling(db_context* ctx, int on);
@@ -223,6 +241,15 @@ db_status db_reset_stats(db_context* ctx);
 db_status db_apply_blur(db_context* ctx, const double* psf_host, int psf_size, int m,
                         db_wavelet wavelet, int level, int transpose,
                         const void* x, void* y, db_precision prec, db_stream stream);
+
+/* *out (host) = sum_i x_i^2 over the n-element device vector x (float64,
+ * float32 or bfloat16 per `prec`), formed by the reduction that gives the
+ * LSQR norms (Sec. 3, the Golub-Kahan scalars alpha and beta): every square
+ * enters exactly (float products with their rounding error recovered by an
+ * FMA), sums are double-float pairs within a 1024-element tile, and the tile
+ * partials are added in tile order. Exposed so that its accuracy against a
+ * float64 reduction can be checked directly. Synchronises `stream`. */
+db_status db_sumsq(const void* x, size_t n, db_precision prec, double* out, db_stream stream);
 
 /* q = L x (two padded planes, 2*m*m) and x = L^T q (Sec. 4.2). */
 db_status db_apply_L(int m, const void* x, void* q, db_precision prec, db_stream stream);
@@ -263,7 +290,10 @@ db_status db_lsqr_solve(db_context* ctx, const double* psf_host, int psf_size, i
  * planes are read in place. The array is shared by every call on a device:
  * calls that overlap in time race on it and must be serialised by the
  * caller. The first call on a device looks the array up; make it before any
- * stream capture begins. Synchronises `stream`. */
+ * stream capture begins. Synchronises `stream`, on success and on error
+ * alike: when the call returns, none of its kernels is still running. A
+ * problem too large for the array is rejected while none of the call's
+ * kernels is in flight. */
 db_status db_lsqr_solve_static(const double* psf_host, int psf_size, int m,
                                db_solver solver, double gamma,
                                const void* b, const void* x0, const void* aux0, const void* aux1,

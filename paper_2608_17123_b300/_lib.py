@@ -26,7 +26,8 @@ class DbOpts(C.Structure):
     _fields_ = [("tol_fine", C.c_double), ("tol_coarse", C.c_double), ("kmax", C.c_int),
                 ("eps_irls", C.c_double), ("eps_mm", C.c_double), ("tau_sb", C.c_double),
                 ("lsqr_atol", C.c_double), ("lsqr_btol", C.c_double), ("lsqr_conlim", C.c_double),
-                ("lsqr_maxit", C.c_int), ("lsqr_warm_start", C.c_int), ("precision", C.c_int)]
+                ("lsqr_maxit", C.c_int), ("lsqr_warm_start", C.c_int), ("precision", C.c_int),
+                ("barrier_timeout_us", C.c_int)]
 
 
 class DbGcvOpts(C.Structure):
@@ -38,7 +39,9 @@ class DbGcvOpts(C.Structure):
 class DbStats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("lsqr_launches", C.c_uint64), ("lsqr_ms", C.c_double),
                 ("lsqr_pixel_iters_irls", C.c_double), ("lsqr_pixel_iters_other", C.c_double),
-                ("gcv_calls", C.c_uint64), ("outer_iterations", C.c_uint64), ("gcv_ms", C.c_double)]
+                ("gcv_calls", C.c_uint64), ("outer_iterations", C.c_uint64), ("gcv_ms", C.c_double),
+                ("lsqr_fine_launches", C.c_uint64), ("lsqr_fine_ms", C.c_double),
+                ("lsqr_fine_pixel_iters_irls", C.c_double), ("lsqr_fine_pixel_iters_other", C.c_double)]
 
 
 class DbRequest(C.Structure):
@@ -74,12 +77,14 @@ _SIGS = {
     "db_server_create": (C.c_int, [_VP, C.POINTER(DbServerOpts), C.POINTER(_VP)]),
     "db_server_submit": (C.c_int, [_VP, C.POINTER(DbRequest), C.POINTER(C.c_uint64)]),
     "db_server_poll": (C.c_int, [_VP, C.c_uint64, C.c_int, C.POINTER(C.c_double)]),
+    "db_server_cancel": (C.c_int, [_VP, C.c_uint64]),
     "db_server_destroy": (C.c_int, [_VP]),
     "db_set_profiling": (C.c_int, [_VP, C.c_int]),
     "db_set_autotune": (C.c_int, [_VP, C.c_int]),
     "db_get_stats": (C.c_int, [_VP, C.POINTER(DbStats)]),
     "db_reset_stats": (C.c_int, [_VP]),
     "db_apply_blur": (C.c_int, [_VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_int, _VP]),
+    "db_sumsq": (C.c_int, [_VP, C.c_size_t, C.c_int, C.POINTER(C.c_double), _VP]),
     "db_apply_L": (C.c_int, [C.c_int, _VP, _VP, C.c_int, _VP]),
     "db_apply_Lt": (C.c_int, [C.c_int, _VP, _VP, C.c_int, _VP]),
     "db_restrict": (C.c_int, [C.c_int, C.c_int, _VP, _VP, C.c_int, _VP]),

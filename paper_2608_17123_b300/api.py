@@ -171,6 +171,16 @@ def apply_blur(psf, m, x, y, level=0, wavelet="haar", transpose=False, ctx=None,
                                   int(transpose), _ptr(x), _ptr(y), _prec(x), _stream(stream)), ctx.handle)
 
 
+def sumsq(x, stream=None):
+    """sum(x^2) of a torch CUDA tensor (float64, float32 or bfloat16) by the
+    library's LSQR-norm reduction (db_sumsq)."""
+    import torch
+    prec = {torch.float64: 0, torch.float32: 1, torch.bfloat16: 2}[x.dtype]
+    out = C.c_double(0.0)
+    L.check(L.lib().db_sumsq(_ptr(x), x.numel(), prec, C.byref(out), _stream(stream)))
+    return out.value
+
+
 def apply_L(m, x, q, stream=None):
     L.check(L.lib().db_apply_L(m, _ptr(x), _ptr(q), _prec(x), _stream(stream)))
 
@@ -264,10 +274,15 @@ class Server:
         st = L.lib().db_server_poll(self.handle, ticket, timeout_us, C.byref(lat))
         if st == 4:  # DB_ETIMEOUT
             return None
+        if st != 0:
+            self._live.pop(ticket, None)
         L.check(st, self.ctx.handle)
         m, x, mu, it, inner, _, _, _ = self._live.pop(ticket)
         return dict(x=from_colmajor(x, m), mu=list(mu), iters=[int(v) for v in it],
                     inner=[int(v) for v in inner]), lat.value
+
+    def cancel(self, ticket):
+        L.check(L.lib().db_server_cancel(self.handle, ticket), self.ctx.handle)
 
     def close(self):
         if self.handle:

@@ -10,9 +10,12 @@ namespace db {
 // ---- storage / accumulation types -----------------------------------------
 // Storage T in {double, float, __nv_bfloat16}; arithmetic Acc is double for
 // double storage and float otherwise. Reductions (norms, dot products) are
-// always finished in double.
-template <typename T> struct Traits { using Acc = float; };
-template <> struct Traits<double> { using Acc = double; };
+// always finished in double. X is the type of the outer iterate x^(k) and of
+// the LSQR correction delta: the accumulating quantities, which stay in Acc
+// when T is bfloat16 (its 8-bit significand would otherwise cap the
+// reconstruction at ~4e-3 relative, whatever the solver does).
+template <typename T> struct Traits { using Acc = float; using X = float; };
+template <> struct Traits<double> { using Acc = double; using X = double; };
 
 __device__ __forceinline__ float to_acc(float v) { return v; }
 __device__ __forceinline__ double to_acc(double v) { return v; }
@@ -92,6 +95,13 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float xh, float xl)
   hi = s;
 }
 
+// (hi, lo) += a * b with the product entered exactly: its rounding error is
+// recovered with one FMA and carried in lo.
+__device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float b) {
+  const float p = a * b;
+  df_add(hi, lo, p, fmaf(a, b, -p));
+}
+
 // (hi, lo) += p[0], p[1], ..., p[n-1] in that order, the loads issued in
 // batches of 8 (L1 bypassed: the partials were written by other blocks), so
 // the chain waits for one memory round trip per batch, not per element.
@@ -121,10 +131,6 @@ __device__ __forceinline__ float2 warp_df_pair(float hi, float lo) {
   }
   return make_float2(hi, lo);
 }
-
-// Kahan-compensated warp dot over strided elements, returned as (hi, lo):
-// acc with Kahan residue -comp, combined across the warp.
-__device__ __forceinline__ float2 warp_df(float acc, float comp) { return warp_df_pair(acc, -comp); }
 
 // Block sum of NV per-thread partials (float or double); the result (double)
 // is valid in thread (0,0) only. `scratch` needs NV * 32 doubles. The warp
@@ -160,10 +166,10 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
-// Grid-wide barrier for cooperative launches, with a time limit. Every block
-// must call it the same number of times. Returns false (in all threads of the
-// block) when the wait timed out or another block already reported a
-// timeout; the caller must then leave the kernel.
+// State of the grid-wide phase barrier of the persistent LSQR launch
+// (lsqr_phase_arrive / lsqr_wait_release): an arrival counter that only
+// grows, the generation published by the block that arrived last, a
+// timeout flag every waiting block checks, and that block's decision.
 struct GridBarrier {
   unsigned int count;
   unsigned int gen;
@@ -171,52 +177,5 @@ struct GridBarrier {
   int decision;   // written by the last block to arrive, read by all after release
 };
 
-// `decide` (if given) runs in the last block to arrive, after every block has
-// finished the phase and before any block is released; its result is
-// returned to all blocks through *decision (no block can start the next phase
-// before it is written).
-template <typename Decide>
-__device__ __forceinline__ bool grid_sync(GridBarrier* gb, unsigned nblocks, uint64_t limit_ns,
-                                          Decide decide, int* decision) {
-  __shared__ int s_ok, s_dec;
-  __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    volatile unsigned int* vgen = &gb->gen;
-    volatile int* verr = &gb->error;
-    int ok = (*verr == 0);
-    if (ok) {
-      unsigned my_gen = *vgen;
-      __threadfence();
-      unsigned arrived = atomicAdd(&gb->count, 1u);
-      if (arrived == nblocks - 1) {
-        gb->decision = decide();
-        gb->count = 0;
-        __threadfence();
-        atomicAdd(&gb->gen, 1u);
-      } else {
-        uint64_t t0 = globaltimer_ns();
-        unsigned spins = 0;
-        while (*vgen == my_gen) {
-          if (*verr) { ok = 0; break; }
-          if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > limit_ns) {
-            atomicExch(&gb->error, 1);
-            ok = 0;
-            break;
-          }
-        }
-      }
-      __threadfence();
-      s_dec = *(volatile int*)&gb->decision;
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  if (decision) *decision = s_dec;
-  return s_ok != 0;
-}
-
-struct NoDecision {
-  __device__ int operator()() const { return 0; }
-};
 
 }  // namespace db

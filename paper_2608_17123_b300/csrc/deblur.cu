@@ -267,6 +267,7 @@ static float lsqr_run(db_context* ctx, cudaStream_t st, const LsqrProb<T, Acc>* 
 template <typename T>
 struct Level {
   using Acc = typename Traits<T>::Acc;
+  using X = typename Traits<T>::X;
   int m = 0;
   size_t n = 0;
   int dlo = 0, w = 0;
@@ -277,9 +278,10 @@ struct Level {
   double* b64 = nullptr;     // right-hand side in double (levels that use the exact GCV)
   // vectors
   T* b = nullptr;
-  T* xa = nullptr;
-  T* xb = nullptr;
-  T *uA = nullptr, *uLx = nullptr, *uLy = nullptr, *v = nullptr, *wv = nullptr, *dlt = nullptr;
+  X* xa = nullptr;           // outer iterate (two ping-pong buffers)
+  X* xb = nullptr;
+  T *uA = nullptr, *uLx = nullptr, *uLy = nullptr, *v = nullptr, *wv = nullptr;
+  X* dlt = nullptr;          // LSQR correction
   T *a0x = nullptr, *a0y = nullptr, *a1x = nullptr, *a1y = nullptr;
   int ntiles_side() const { return (m + TM - 1) / TM; }
   BandOp<Acc> op(int nterms) const {
@@ -340,6 +342,8 @@ struct GcvBufs {
   size_t gwork_cap = 0;               // doubles in gwork
   float2* gpart2 = nullptr;
   size_t gpart2_cap = 0;
+  float* gsk = nullptr;               // block partials of k_gram_dtd
+  size_t gsk_blocks = 0;              // blocks they have room for
   int gkmax = 0;
   size_t gn = 0;
   // Krylov basis K_k(A^T A, A^T b) of the projected GCV, kept between calls on
@@ -357,9 +361,12 @@ struct GcvBufs {
     size_t tot = n0 * sizeof(Acc) * (kmax + 9);
     tot += (size_t)kmax * kmax * sizeof(double) * 8 + (size_t)kmax * 4096 * sizeof(double);
     tot += (size_t)exact_max * exact_max * sizeof(double) + (size_t)kmax * 160 * sizeof(double);
-    tot += (size_t)std::max(2 * kmax + 4, (kmax + 1) * GDB_NB) * std::max<size_t>((n0 + 2047) / 2048, (size_t)4 * nsm) * 8;
+    tot += (size_t)(2 * kmax + 4) * std::max<size_t>((n0 + 2047) / 2048, (size_t)4 * nsm) * 8;
+    tot += sk_blocks(nsm) * SK_SLOTS * sizeof(float);
     return tot + 64 * 4096 + 1024;
   }
+
+  static size_t sk_blocks(int nsm) { return (size_t)2 * nsm + 8; }
 
   void alloc(Arena& A, size_t n0, int kmax, int exact_max, int nsm) {
     gkmax = kmax;
@@ -385,15 +392,18 @@ struct GcvBufs {
     kc_epoch = 0;
     kc_cols = 0;
     const size_t nch = std::max<size_t>((n0 + VCH_CHUNK - 1) / VCH_CHUNK, (size_t)4 * nsm);
-    gpart2_cap = (size_t)std::max(2 * kmax + 4, (kmax + 1) * GDB_NB) * nch;
+    gpart2_cap = (size_t)(2 * kmax + 4) * nch;
     gpart2 = A.take<float2>(gpart2_cap);
     gmdot_part = A.take<double>((size_t)kmax * 256);
+    gsk_blocks = sk_blocks(nsm);
+    gsk = A.take<float>(gsk_blocks * SK_SLOTS);
   }
 };
 
 template <typename T>
 struct Engine {
   using Acc = typename Traits<T>::Acc;
+  using X = typename Traits<T>::X;
   db_context* ctx;
   cudaStream_t st;
   Hierarchy<T> H;
@@ -421,6 +431,8 @@ struct Engine {
   size_t gwork_cap = 0;
   float2* gpart2 = nullptr;
   size_t gpart2_cap = 0;
+  float* gsk = nullptr;
+  size_t gsk_blocks = 0;
   int gkmax = 0;
   size_t gn = 0;
 
@@ -433,7 +445,7 @@ struct Engine {
     gV = b.gV; gt = b.gt; gz = b.gz; gy = b.gy; gatb = b.gatb; gdtc = b.gdtc; gknext = b.gknext;
     gcx = b.gcx; gcy = b.gcy; gGA = b.gGA; gGD = b.gGD; ggA = b.ggA; ggD = b.ggD; gh = b.gh; gwork = b.gwork;
     gmdot_part = b.gmdot_part; gAd = b.gAd; gbA = b.gbA; gbD = b.gbD; gh2 = b.gh2; gtrt = b.gtrt; gwork_cap = b.gwork_cap; gpart2 = b.gpart2;
-    gpart2_cap = b.gpart2_cap; gkmax = b.gkmax; gn = b.gn;
+    gpart2_cap = b.gpart2_cap; gkmax = b.gkmax; gn = b.gn; gsk = b.gsk; gsk_blocks = b.gsk_blocks;
   }
 
   Engine(db_context* c, cudaStream_t s) : ctx(c), st(s) {}
@@ -448,7 +460,7 @@ struct Engine {
     for (int i = 0; i < levels; ++i) {
       int mi = m >> i;
       size_t n = (size_t)mi * mi;
-      tot += n * sizeof(T) * 16 + n * sizeof(float) + n * sizeof(double);
+      tot += n * (sizeof(T) * 16 + sizeof(X) * 3) + n * sizeof(float) + n * sizeof(double);
       tot += (size_t)mi * (S + 64) * (sizeof(double) * 2 + sizeof(Acc) * 4) * S + 4096;
       tot += (size_t)4 * S * m * 16;
     }
@@ -537,9 +549,9 @@ struct Engine {
         { count_launch(); k_symbol_rho<<<grid_for(n, ctx->nsm), 256, 0, st>>>(L.m, nterms, Kr, Kc, L.rho); }
         CK(cudaGetLastError());
         L.b = A.take<T>(n);
-        L.xa = A.take<T>(n); L.xb = A.take<T>(n);
+        L.xa = A.take<X>(n); L.xb = A.take<X>(n);
         L.uA = A.take<T>(n); L.uLx = A.take<T>(n); L.uLy = A.take<T>(n);
-        L.v = A.take<T>(n); L.wv = A.take<T>(n); L.dlt = A.take<T>(n);
+        L.v = A.take<T>(n); L.wv = A.take<T>(n); L.dlt = A.take<X>(n);
         L.a0x = A.take<T>(n); L.a0y = A.take<T>(n); L.a1x = A.take<T>(n); L.a1y = A.take<T>(n);
       }
     }
@@ -628,7 +640,7 @@ struct Engine {
   }
 
   // ---------------------------------------------------------------- LSQR
-  int lsqr(const Level<T>& L, int solver, double gamma, const T* x0, int* stop_out = nullptr) {
+  int lsqr(const Level<T>& L, int solver, double gamma, const X* x0, int* stop_out = nullptr) {
     LsqrProb<T, Acc> P;
     P.op = L.op(H.nterms);
     P.m = L.m;
@@ -649,7 +661,7 @@ struct Engine {
     c.atol = o.lsqr_atol; c.btol = o.lsqr_btol; c.conlim = o.lsqr_conlim; c.maxit = o.lsqr_maxit;
     c.nprob = 1; c.ntiles = P.ntiles;
     c.tile_prob = d_tile_prob; c.part = d_part; c.cnt = d_cnt; c.st = d_st; c.gb = d_gb; c.coef = d_coef;
-    c.limit_ns = 2000000000ull;
+    c.limit_ns = (unsigned long long)o.barrier_timeout_us * 1000ull;
     auto reset = [&]() {
       CK(cudaMemsetAsync(d_st, 0, sizeof(LsqrState), st));
       CK(cudaMemsetAsync(d_coef, 0, sizeof(LsqrCoef<Acc>), st));
@@ -669,6 +681,12 @@ struct Engine {
     if (solver == DB_IRLS) ctx->stats.lsqr_pixel_iters_irls += pix;
     else ctx->stats.lsqr_pixel_iters_other += pix;
     if (ctx->profiling) ctx->stats.lsqr_ms += lsqr_ms;
+    if (!H.lv.empty() && &L == &H.lv[0]) {
+      ctx->stats.lsqr_fine_launches++;
+      if (solver == DB_IRLS) ctx->stats.lsqr_fine_pixel_iters_irls += pix;
+      else ctx->stats.lsqr_fine_pixel_iters_other += pix;
+      if (ctx->profiling) ctx->stats.lsqr_fine_ms += lsqr_ms;
+    }
     return S.its;
   }
 
@@ -981,6 +999,24 @@ struct Engine {
     part_reduce(2 * (nr + 2), nch, gpart2, RedGramCol{nr, jout, gkmax, t != nullptr ? 1 : 0, gGA, gGD, ggA, ggD});
   }
 
+  // G_D[i][j], i <= j < kk, of V_0..V_{kk-1} for the weights (wx, wy) (null:
+  // unweighted): k_gram_dtd over ~2 blocks per SM, then k_gram_dtd_reduce
+  void gram_dtd(int m, int kk, const float* V, const T* wx, const T* wy, int ld) {
+    REQUIRE(kk >= 1 && kk <= SK_KMAX, "G_D kernel takes at most 165 basis vectors");
+    const size_t n = (size_t)m * m;
+    size_t ppb = (n + (size_t)2 * ctx->nsm - 1) / ((size_t)2 * ctx->nsm);
+    ppb = std::max<size_t>((ppb + SK_PC - 1) / SK_PC * SK_PC, SK_PC);
+    const size_t nblk = (n + ppb - 1) / ppb;
+    REQUIRE(nblk <= gsk_blocks, "G_D partial buffer too small");
+    count_launch();
+    k_gram_dtd<T><<<(unsigned)nblk, SK_THREADS, 0, st>>>(m, kk, V, wx, wy, (int)ppb, gsk);
+    const int nb = (kk + SK_TI - 1) / SK_TI;
+    const int nslot = nb * (nb + 1) / 2 * SK_TI * SK_TI;
+    count_launch();
+    k_gram_dtd_reduce<<<(nslot + 31) / 32, 256, 0, st>>>((int)nblk, kk, gsk, gGD, ld);
+    CK(cudaGetLastError());
+  }
+
   double gcv_projected_fused(const Level<T>& L, const T* wx, const T* wy, bool has_c, double s, double bnorm2,
                              double atb2, bool kc_hit) {
     const size_t n = L.n;
@@ -1020,20 +1056,6 @@ struct Engine {
       if (2 * k > kcap || k >= (int)n) break;
     }
     const int ktop = seq.back();
-    // G_D, g_D of cached columns for the current weights and shift, GDB_NB
-    // columns per launch (the chunk size is the one the Krylov kernels use)
-    const int ncached = std::min(ktop, cached);
-    for (int j0 = 0; j0 < ncached; j0 += GDB_NB) {
-      const int nb = std::min(GDB_NB, ncached - j0);
-      const size_t need = (size_t)(j0 + nb + 1) * nb * nch;
-      REQUIRE(need <= gpart2_cap, "Gram partial buffer too small");
-      const size_t smb = (size_t)nb * E * VCH_THREADS * sizeof(float);
-      if (smb > 48 * 1024) CK(cudaFuncSetAttribute(k_gram_dcols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
-      count_launch();
-      k_gram_dcols<T><<<nch, VCH_THREADS, smb, st>>>(m, j0, nb, V, wx, wy, dtcf, gpart2, E);
-      part_reduce((j0 + nb + 1) * nb, nch, gpart2, RedDcols{j0, nb, ld, gGD, ggD});
-    }
-    CK(cudaGetLastError());
     // new columns: v_j = t / ||t|| (written by the A pass), z = A v_j, t = A^T z
     while (C.kc_cols < ktop) {
       const int j = C.kc_cols;
@@ -1049,6 +1071,13 @@ struct Engine {
       }
       CK(cudaGetLastError());
     }
+    // G_D and g_D of the basis columns for the current weights and shift, in
+    // one pass over V (the same arithmetic whether the columns were cached or
+    // have just been built)
+    gram_dtd(m, ktop, V, wx, wy, ld);
+    if (dtcf) vchunk(n, ktop, V, nullptr, 0, const_cast<float*>(dtcf), VCH_DOTS, ggD, 1, nullptr, nch, E);
+    else CK(cudaMemsetAsync(ggD, 0, (size_t)ktop * sizeof(double), st));
+    CK(cudaGetLastError());
     // selections in groups of up to three per launch, the doubling rule
     // (stop at the first dimension whose gamma agrees with the previous one
     // to 0.1 %) applied in sequence order
@@ -1102,7 +1131,7 @@ struct Engine {
 
   // ---------------------------------------------------------------- outer step
   // x_new = x_old + delta, auxiliaries from L x_new; returns RC.
-  double outer_update(Level<T>& L, int solver, const T* x_old, T* x_new) {
+  double outer_update(Level<T>& L, int solver, const X* x_old, X* x_new) {
     const size_t n = L.n;
     const int g = grid_for(n, ctx->nsm);
     { count_launch(); k_outer_update<T><<<g, 256, 0, st>>>(L.m, solver, o.lsqr_warm_start, x_old, L.dlt, x_new, L.a0x, L.a0y,
@@ -1116,8 +1145,8 @@ struct Engine {
 
   // one level of Alg. 4 (Alg. 1/2/3 inside); x in L.xa on entry and exit
   void level_solve(Level<T>& L, int solver, double tol, bool twopass, double* mu, int* iters, int* inner) {
-    T* x = L.xa;
-    T* xn = L.xb;
+    X* x = L.xa;
+    X* xn = L.xb;
     double gamma = 0.0;
     int k = 0, tot_inner = 0;
     for (k = 0; k < o.kmax; ++k) {
@@ -1136,7 +1165,7 @@ struct Engine {
       if (rc < tol) { ++k; break; }
     }
     if (k > o.kmax) k = o.kmax;
-    if (x != L.xa) CK(cudaMemcpyAsync(L.xa, x, L.n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    if (x != L.xa) CK(cudaMemcpyAsync(L.xa, x, L.n * sizeof(X), cudaMemcpyDeviceToDevice, st));
     *mu = gamma;
     *iters = k;
     *inner = tot_inner;
@@ -1150,17 +1179,17 @@ struct Engine {
     Level<T>& L = H.lv[i];
     const int g = grid_for(L.n, ctx->nsm);
     if (i == H.levels - 1) {
-      { count_launch(); k_fill<T><<<g, 256, 0, st>>>(L.n, L.xa, 0.0); }
+      { count_launch(); k_fill<X><<<g, 256, 0, st>>>(L.n, L.xa, 0.0); }
       { count_launch(); k_aux_init<T><<<g, 256, 0, st>>>(L.m, solver, AUX_APPROACH_I, L.xa, L.a0x, L.a0y, L.a1x,
             L.a1y, o.eps_irls, o.eps_mm, o.tau_sb); }
     } else {
       const Level<T>& C = H.lv[i + 1];
       if (tr == DB_APPROACH_X) {
-        { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.xa, L.xa, 0, 0); }
+        { count_launch(); k_prolong<X><<<g, 256, 0, st>>>(C.m, f, C.xa, L.xa, 0, 0); }
         { count_launch(); k_aux_init<T><<<g, 256, 0, st>>>(L.m, solver, AUX_FROM_X, L.xa, L.a0x, L.a0y, L.a1x,
               L.a1y, o.eps_irls, o.eps_mm, o.tau_sb); }
       } else {
-        { count_launch(); k_fill<T><<<g, 256, 0, st>>>(L.n, L.xa, 0.0); }
+        { count_launch(); k_fill<X><<<g, 256, 0, st>>>(L.n, L.xa, 0.0); }
         { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.a0x, L.a0x, 1, 0); }
         { count_launch(); k_prolong<T><<<g, 256, 0, st>>>(C.m, f, C.a0y, L.a0y, 0, 1); }
         if (solver == DB_SB) {
@@ -1184,7 +1213,7 @@ struct Engine {
 
   // x_new = x_old + delta and auxiliaries, without waiting; the two RC norms
   // land in out[0..1].
-  void outer_update_async(Level<T>& L, int solver, const T* x_old, T* x_new, double* out) {
+  void outer_update_async(Level<T>& L, int solver, const X* x_old, X* x_new, double* out) {
     const int g = grid_for(L.n, ctx->nsm);
     { count_launch(); k_outer_update<T><<<g, 256, 0, st>>>(L.m, solver, o.lsqr_warm_start, x_old, L.dlt, x_new,
           L.a0x, L.a0y, L.a1x, L.a1y, o.eps_irls, o.eps_mm, o.tau_sb, d_part, d_cnt + 4, out); }
@@ -1199,6 +1228,7 @@ struct Engine {
 template <typename T>
 struct BatchSolver {
   using Acc = typename Traits<T>::Acc;
+  using X = typename Traits<T>::X;
   struct Prob {
     std::unique_ptr<Engine<T>> E;
     db_solver solver;
@@ -1207,8 +1237,8 @@ struct BatchSolver {
     int levels = 0, level = 0, k = 0, inner = 0;
     double gamma = 0.0;
     bool done = false;
-    T* x = nullptr;
-    T* xn = nullptr;
+    X* x = nullptr;
+    X* xn = nullptr;
     std::vector<double> mu;
     std::vector<int> iters, inners;
   };
@@ -1387,7 +1417,7 @@ struct BatchSolver {
     c.atol = o.lsqr_atol; c.btol = o.lsqr_btol; c.conlim = o.lsqr_conlim; c.maxit = o.lsqr_maxit;
     c.nprob = np; c.ntiles = (int)tp.size();
     c.tile_prob = d_tile_prob; c.part = d_part; c.cnt = nullptr; c.st = d_states; c.gb = d_gb; c.coef = d_coefs;
-    c.limit_ns = 2000000000ull;
+    c.limit_ns = (unsigned long long)o.barrier_timeout_us * 1000ull;
     std::vector<BandOp<Acc>> ops(np);
     for (int j = 0; j < np; ++j) ops[j] = hp[j].op;
     auto reset = [&]() {
@@ -1445,7 +1475,7 @@ struct BatchSolver {
       const double tol = q.level > 0 ? o.tol_coarse : o.tol_fine;
       if (r < tol || q.k >= o.kmax) {
         Level<T>& L = q.E->H.lv[q.level];
-        if (q.x != L.xa) CK(cudaMemcpyAsync(L.xa, q.x, L.n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        if (q.x != L.xa) CK(cudaMemcpyAsync(L.xa, q.x, L.n * sizeof(X), cudaMemcpyDeviceToDevice, st));
         q.mu[q.level] = q.gamma;
         q.iters[q.level] = q.k;
         q.inners[q.level] = q.inner;
@@ -1480,6 +1510,7 @@ extern "C" void db_default_opts(db_opts* o, db_gcv_opts* g) {
     o->eps_irls = 0.03; o->eps_mm = 0.03; o->tau_sb = 0.005;
     o->lsqr_atol = 1e-6; o->lsqr_btol = 1e-6; o->lsqr_conlim = 1e8; o->lsqr_maxit = 100;
     o->lsqr_warm_start = 1; o->precision = DB_PREC_FP32;
+    o->barrier_timeout_us = 2000000;
   }
   if (g) {
     g->grid_points = 50; g->log10_gamma_lo = -10.0; g->log10_gamma_hi = 2.0;
@@ -1578,6 +1609,14 @@ static void validate(int m, int S, int levels, db_wavelet wv) {
   REQUIRE((m >> (levels - 1)) >= kappa && (m >> (levels - 1)) >= 2, "coarsest level smaller than the filter");
 }
 
+static void validate_opts(const db_opts& o, const db_gcv_opts& g) {
+  REQUIRE(g.proj_dim >= 1 && g.proj_dim_max >= g.proj_dim && g.grid_points >= 3 && g.grid_points <= 64,
+          "bad GCV options");
+  REQUIRE(g.exact_max_pixels >= 0 && g.exact_max_pixels <= 1024, "exact_max_pixels out of range");
+  REQUIRE(o.kmax >= 1 && o.lsqr_maxit >= 1, "bad iteration limits");
+  REQUIRE(o.barrier_timeout_us >= 0, "barrier_timeout_us must be >= 0");
+}
+
 template <typename T>
 static void run_solve(db_context* ctx, cudaStream_t st, const double* b_dev, int m, const double* psf_dev, int S,
                       db_solver solver, db_wavelet wv, int levels, db_transfer tr, const db_gcv_opts& g,
@@ -1589,7 +1628,7 @@ static void run_solve(db_context* ctx, cudaStream_t st, const double* b_dev, int
   ctx->arena.reset();
   E.build(psf_dev, S, m, levels, wv, b_dev, true);
   E.vcycle(solver, wv, levels == 1 ? DB_APPROACH_I : tr, mu, iters, inner);
-  { count_launch(); k_convert_out<T><<<grid_for((size_t)m * m, ctx->nsm), 256, 0, st>>>((size_t)m * m, E.H.lv[0].xa, x_dev); }
+  { count_launch(); k_convert_out<typename Traits<T>::X><<<grid_for((size_t)m * m, ctx->nsm), 256, 0, st>>>((size_t)m * m, E.H.lv[0].xa, x_dev); }
   CK(cudaGetLastError());
 }
 
@@ -1599,6 +1638,8 @@ extern "C" db_status deblur_solve(db_context* ctx, const double* b, int m, const
                        int* inner_iters_per_level, int on_device, db_stream stream) {
   if (!ctx) return DB_EINVAL;
   CountScope count_scope(ctx);
+  cudaStream_t st = (cudaStream_t)stream;
+  double *db_ = nullptr, *dpsf = nullptr, *dx = nullptr;   // staging copies of host arguments
   try {
     REQUIRE(b && psf && x && mu_per_level && iters_per_level, "null pointer argument");
     validate(m, S, levels, wavelet);
@@ -1609,15 +1650,9 @@ extern "C" db_status deblur_solve(db_context* ctx, const double* b, int m, const
     db_default_opts(&o, &g);
     if (opts) o = *opts;
     if (gcv) g = *gcv;
-    REQUIRE(g.proj_dim >= 1 && g.proj_dim_max >= g.proj_dim && g.grid_points >= 3 && g.grid_points <= 64,
-            "bad GCV options");
-    REQUIRE(g.exact_max_pixels >= 0 && g.exact_max_pixels <= 1024, "exact_max_pixels out of range");
-    REQUIRE(o.kmax >= 1 && o.lsqr_maxit >= 1, "bad iteration limits");
+    validate_opts(o, g);
     CK(cudaSetDevice(ctx->device));
-    cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)m * m;
-    double *db_ = nullptr, *dpsf = nullptr, *dx = nullptr;
-    std::vector<double> hx;
     if (!on_device) {
       CK(cudaMallocAsync((void**)&db_, n * sizeof(double), st));
       CK(cudaMallocAsync((void**)&dpsf, (size_t)S * S * sizeof(double), st));
@@ -1642,6 +1677,7 @@ extern "C" db_status deblur_solve(db_context* ctx, const double* b, int m, const
       CK(cudaFreeAsync(db_, st));
       CK(cudaFreeAsync(dpsf, st));
       CK(cudaFreeAsync(dx, st));
+      db_ = dpsf = dx = nullptr;
     }
     CK(cudaStreamSynchronize(st));
     for (int i = 0; i < levels; ++i) {
@@ -1651,6 +1687,14 @@ extern "C" db_status deblur_solve(db_context* ctx, const double* b, int m, const
     }
     return DB_OK;
   } catch (DbError& e) {
+    // nothing of this call may still run, or hold memory, when it returns
+    cudaStreamSynchronize(st);
+    if (!on_device) {
+      if (db_) cudaFree(db_);
+      if (dpsf) cudaFree(dpsf);
+      if (dx) cudaFree(dx);
+    }
+    cudaGetLastError();
     ctx->err = e.msg;
     return e.st;
   }
@@ -1670,7 +1714,7 @@ static void run_batch(db_context* ctx, cudaStream_t st, int count, const db_requ
   for (int i = 0; i < count; ++i) {
     auto& q = B.P[i];
     const size_t n = (size_t)reqs[i].m * reqs[i].m;
-    { count_launch(); k_convert_out<T><<<grid_for(n, ctx->nsm), 256, 0, st>>>(n, q.E->H.lv[0].xa, x_dev[i]); }
+    { count_launch(); k_convert_out<typename Traits<T>::X><<<grid_for(n, ctx->nsm), 256, 0, st>>>(n, q.E->H.lv[0].xa, x_dev[i]); }
     for (int l = 0; l < q.levels; ++l) {
       reqs[i].mu_per_level[l] = q.mu[l];
       reqs[i].iters_per_level[l] = q.iters[l];
@@ -1693,8 +1737,7 @@ extern "C" db_status deblur_solve_batch(db_context* ctx, int count, const db_req
     db_default_opts(&o, &g);
     if (opts) o = *opts;
     if (gcv) g = *gcv;
-    REQUIRE(g.proj_dim >= 1 && g.proj_dim_max >= g.proj_dim && g.grid_points >= 3 && g.grid_points <= 64,
-            "bad GCV options");
+    validate_opts(o, g);
     for (int i = 0; i < count; ++i) {
       const db_request& r = reqs[i];
       REQUIRE(r.b && r.psf && r.x && r.mu_per_level && r.iters_per_level, "null pointer in a request");
@@ -1753,6 +1796,7 @@ struct ServerJob {
   size_t bytes = 0;
   int slot = -1;
   bool done = false;
+  bool cancel = false;               // withdrawn while resident: retired at the next step boundary
   db_status status = DB_OK;
   std::chrono::steady_clock::time_point t_submit, t_done;
 };
@@ -1785,6 +1829,20 @@ struct db_server {
       // admission at a step boundary
       {
         std::unique_lock<std::mutex> lk(mu);
+        // resident requests withdrawn by db_server_cancel leave first
+        for (int i = 0; i < (int)slots.size(); ++i) {
+          ServerJob* j = slots[i];
+          if (!j || !j->cancel) continue;
+          B->P[i].done = true;
+          B->P[i].E.reset();
+          j->arena.reset();
+          bytes_in_use -= j->bytes;
+          slots[i] = nullptr;
+          j->status = DB_ECANCELLED;
+          j->done = true;
+          j->t_done = std::chrono::steady_clock::now();
+          cv_done.notify_all();
+        }
         bool any_resident = false;
         for (auto* j : slots) any_resident |= (j != nullptr);
         if (!any_resident && queue.empty()) {
@@ -1882,6 +1940,7 @@ extern "C" db_status db_server_create(db_context* ctx, const db_server_opts* o, 
   try {
     REQUIRE(o->max_resident >= 1 && o->max_resident <= 256, "max_resident out of range");
     REQUIRE(o->max_m >= 8 && (o->max_m & (o->max_m - 1)) == 0, "max_m must be a power of two");
+    validate_opts(o->opts, o->gcv);
     CK(cudaSetDevice(ctx->device));
     std::unique_ptr<db_server> s(new db_server());
     s->ctx = ctx;
@@ -1951,6 +2010,26 @@ extern "C" db_status db_server_poll(db_server* s, uint64_t ticket, int timeout_u
   return j->status;
 }
 
+extern "C" db_status db_server_cancel(db_server* s, uint64_t ticket) {
+  if (!s) return DB_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(ticket);
+  if (it == s->jobs.end()) return DB_EINVAL;
+  ServerJob* j = it->second.get();
+  if (j->done) return DB_OK;                    // finished already: nothing to withdraw
+  auto q = std::find(s->queue.begin(), s->queue.end(), j);
+  if (q != s->queue.end()) {                    // not admitted yet: leaves the queue at once
+    s->queue.erase(q);
+    j->status = DB_ECANCELLED;
+    j->done = true;
+    j->t_done = std::chrono::steady_clock::now();
+    s->cv_done.notify_all();
+  } else {
+    j->cancel = true;                           // resident: the scheduler retires it
+  }
+  return DB_OK;
+}
+
 extern "C" db_status db_server_destroy(db_server* s) {
   if (!s) return DB_EINVAL;
   {
@@ -2016,6 +2095,60 @@ static int dev_sms() {
   cudaGetDevice(&d);
   cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
   return n > 0 ? n : 1;
+}
+
+// Sum of squares through the reduction of the LSQR norms: each thread
+// accumulates the squares of its PIX elements of a 1024-element tile
+// (Sums3), tile_partial combines the block, problem_partials adds the tile
+// partials in tile order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sumsq_tiles(size_t n, const T* __restrict__ x, double* __restrict__ part) {
+  using Acc = typename Traits<T>::Acc;
+  __shared__ double scratch[3 * 32];
+  Sums3<Acc> red;
+  const size_t base = (size_t)blockIdx.x * (TM * TN);
+#pragma unroll
+  for (int j = 0; j < PIX; ++j) {
+    const size_t i = base + threadIdx.x + (size_t)TM * pix_col(j);
+    if (i < n) red.sq(0, to_acc(x[i]));
+  }
+  tile_partial(red, part + (size_t)blockIdx.x * 3, scratch);
+}
+template <typename Acc>
+__global__ void k_sumsq_finish(int ntiles, const double* __restrict__ part, double* __restrict__ out) {
+  double tot[3];
+  problem_partials<Acc>(part, ntiles, tot);
+  if (threadIdx.x == 0) *out = tot[0];
+}
+
+extern "C" db_status db_sumsq(const void* x, size_t n, db_precision prec, double* out, db_stream stream) {
+  return simple_call([&] {
+    REQUIRE(x && out && n >= 1, "bad arguments");
+    REQUIRE(prec == DB_PREC_FP64 || prec == DB_PREC_FP32 || prec == DB_PREC_BF16, "unknown precision");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t ntiles = (n + TM * TN - 1) / (TM * TN);
+    REQUIRE(ntiles <= (size_t)INT32_MAX, "vector too long");
+    double* d = nullptr;
+    CK(cudaMallocAsync((void**)&d, (ntiles * 3 + 1) * sizeof(double), st));
+    const dim3 blk(32, TY);
+    if (prec == DB_PREC_FP64) {
+      k_sumsq_tiles<double><<<(unsigned)ntiles, blk, 0, st>>>(n, (const double*)x, d);
+      k_sumsq_finish<double><<<1, 32, 0, st>>>((int)ntiles, d, d + ntiles * 3);
+    } else if (prec == DB_PREC_FP32) {
+      k_sumsq_tiles<float><<<(unsigned)ntiles, blk, 0, st>>>(n, (const float*)x, d);
+      k_sumsq_finish<float><<<1, 32, 0, st>>>((int)ntiles, d, d + ntiles * 3);
+    } else {
+      k_sumsq_tiles<__nv_bfloat16><<<(unsigned)ntiles, blk, 0, st>>>(n, (const __nv_bfloat16*)x, d);
+      k_sumsq_finish<float><<<1, 32, 0, st>>>((int)ntiles, d, d + ntiles * 3);
+    }
+    count_launch();
+    count_launch();
+    const cudaError_t e = cudaGetLastError();
+    CK(cudaMemcpyAsync(out, d + ntiles * 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaFreeAsync(d, st));
+    CK(cudaStreamSynchronize(st));
+    CK(e);
+  });
 }
 
 extern "C" db_status db_apply_L(int m, const void* x, void* q, db_precision prec, db_stream stream) {
@@ -2297,7 +2430,9 @@ static void static_lsqr(cudaStream_t st, const double* psf_host, int S, int m, d
   CK(cudaMemcpyAsync(&nterms, d_nt, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   REQUIRE(nterms >= 1, "PSF is zero");
-  // level-0 bands (zero-boundary blur, Sec. 5)
+  // Every remaining piece of the workspace is carved out before the next
+  // launch, so an input too large for the array is rejected (DB_EINVAL)
+  // while no kernel of this call is in flight.
   Level<T> L;
   L.m = m;
   L.n = n;
@@ -2307,34 +2442,15 @@ static void static_lsqr(cudaStream_t st, const double* psf_host, int S, int m, d
   L.Bd_r = cur.take<double>(nb);
   L.Bd_c = cur.take<double>(nb);
   L.br = cur.take<Acc>(nb); L.bc = cur.take<Acc>(nb); L.brT = cur.take<Acc>(nb); L.bcT = cur.take<Acc>(nb);
-  const int gb = grid_for(nb, nsm);
-  k_fine_bands_d<<<gb, 256, 0, st>>>(m, S, nterms, fr, L.Bd_r);
-  k_fine_bands_d<<<gb, 256, 0, st>>>(m, S, nterms, fc, L.Bd_c);
-  k_transpose_band<Acc><<<gb, 256, 0, st>>>(m, L.dlo, L.w, nterms, L.Bd_r, L.br, L.brT);
-  k_transpose_band<Acc><<<gb, 256, 0, st>>>(m, L.dlo, L.w, nterms, L.Bd_c, L.bc, L.bcT);
-  CK(cudaGetLastError());
   // LSQR vectors; the caller's b, x0 and auxiliary planes are read in place
   L.uA = cur.take<T>(n); L.uLx = cur.take<T>(n); L.uLy = cur.take<T>(n);
   L.v = cur.take<T>(n); L.wv = cur.take<T>(n); L.dlt = cur.take<T>(n);
-  const int gn = grid_for(n, nsm);
-  T* zeros = nullptr;     // x0 / shift planes the caller left out
-  T* ones = nullptr;      // unit IRLS weights
-  auto zero_plane = [&]() {
-    if (!zeros) { zeros = cur.take<T>(n); k_fill<T><<<gn, 256, 0, st>>>(n, zeros, 0.0); }
-    return zeros;
-  };
   const T* a0 = static_cast<const T*>(aux0);
   const T* a1 = static_cast<const T*>(aux1);
-  if (a0) { L.a0x = const_cast<T*>(a0); L.a0y = const_cast<T*>(a0) + n; }
-  else if (solver == DB_IRLS) {
-    ones = cur.take<T>(n);
-    k_fill<T><<<gn, 256, 0, st>>>(n, ones, 1.0);
-    L.a0x = L.a0y = ones;
-  } else { L.a0x = L.a0y = zero_plane(); }
-  if (a1) { L.a1x = const_cast<T*>(a1); L.a1y = const_cast<T*>(a1) + n; }
-  else { L.a1x = L.a1y = zero_plane(); }
-  const T* xstart = x0 ? static_cast<const T*>(x0) : zero_plane();
-  CK(cudaGetLastError());
+  const bool need_ones = !a0 && solver == DB_IRLS;                     // unit IRLS weights
+  const bool need_zeros = (!a0 && solver != DB_IRLS) || !a1 || !x0;    // planes the caller left out
+  T* ones = need_ones ? cur.take<T>(n) : nullptr;
+  T* zeros = need_zeros ? cur.take<T>(n) : nullptr;
   // LSQR control block; the state, coefficients, tile counters and the grid
   // barrier must start at zero
   const int nt = L.ntiles_side();
@@ -2347,6 +2463,23 @@ static void static_lsqr(cudaStream_t st, const double* psf_host, int S, int m, d
   LsqrCoef<Acc>* d_coef = cur.take<LsqrCoef<Acc>>(1);
   LsqrProb<T, Acc>* d_prob = cur.take<LsqrProb<T, Acc>>(1);
   int* d_tile_prob = cur.take<int>(ntiles);
+  // level-0 bands (zero-boundary blur, Sec. 5)
+  const int gb = grid_for(nb, nsm);
+  k_fine_bands_d<<<gb, 256, 0, st>>>(m, S, nterms, fr, L.Bd_r);
+  k_fine_bands_d<<<gb, 256, 0, st>>>(m, S, nterms, fc, L.Bd_c);
+  k_transpose_band<Acc><<<gb, 256, 0, st>>>(m, L.dlo, L.w, nterms, L.Bd_r, L.br, L.brT);
+  k_transpose_band<Acc><<<gb, 256, 0, st>>>(m, L.dlo, L.w, nterms, L.Bd_c, L.bc, L.bcT);
+  CK(cudaGetLastError());
+  const int gn = grid_for(n, nsm);
+  if (ones) k_fill<T><<<gn, 256, 0, st>>>(n, ones, 1.0);
+  if (zeros) k_fill<T><<<gn, 256, 0, st>>>(n, zeros, 0.0);
+  if (a0) { L.a0x = const_cast<T*>(a0); L.a0y = const_cast<T*>(a0) + n; }
+  else if (solver == DB_IRLS) { L.a0x = L.a0y = ones; }
+  else { L.a0x = L.a0y = zeros; }
+  if (a1) { L.a1x = const_cast<T*>(a1); L.a1y = const_cast<T*>(a1) + n; }
+  else { L.a1x = L.a1y = zeros; }
+  const T* xstart = x0 ? static_cast<const T*>(x0) : zeros;
+  CK(cudaGetLastError());
   CK(cudaMemsetAsync(d_cnt, 0, 64 * sizeof(unsigned), st));
   CK(cudaMemsetAsync(d_gb, 0, sizeof(GridBarrier), st));
   CK(cudaMemsetAsync(d_st, 0, sizeof(LsqrState), st));
@@ -2370,7 +2503,7 @@ static void static_lsqr(cudaStream_t st, const double* psf_host, int S, int m, d
   c.atol = o.lsqr_atol; c.btol = o.lsqr_btol; c.conlim = o.lsqr_conlim; c.maxit = o.lsqr_maxit;
   c.nprob = 1; c.ntiles = ntiles;
   c.tile_prob = d_tile_prob; c.part = d_part; c.cnt = d_cnt; c.st = d_st; c.gb = d_gb; c.coef = d_coef;
-  c.limit_ns = 2000000000ull;
+  c.limit_ns = (unsigned long long)o.barrier_timeout_us * 1000ull;
   c.band_cache = 0;
   c.band_pw = 0;
   c.cache_off = 0;
@@ -2418,6 +2551,10 @@ extern "C" db_status db_lsqr_solve_static(const double* psf_host, int S, int m, 
     else REQUIRE(false, "FP64 or FP32 only");
     return DB_OK;
   } catch (DbError& e) {
+    // kernels of this call may already be queued: wait for them, so that the
+    // static array is idle when the error returns (the documented contract)
+    cudaStreamSynchronize((cudaStream_t)stream);
+    cudaGetLastError();
     g_last_error = e.msg;
     return e.st;
   }

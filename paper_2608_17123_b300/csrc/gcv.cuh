@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(VCH_THREADS) k_vchunk(size_t n, int nrows, con
   if (mode & VCH_UPDATE)
     for (int i = tid; i < nrows; i += VCH_THREADS) cs[i] = (float)coef[(size_t)i * cstride];
   __syncthreads();
-  float nacc = 0.f, ncomp = 0.f;
+  float nhi = 0.f, nlo = 0.f;
   for (int k = 0; k < E; ++k) {
     const int le = k * VCH_THREADS + tid;
     const size_t e = beg + le;
@@ -178,10 +178,7 @@ __global__ void __launch_bounds__(VCH_THREADS) k_vchunk(size_t n, int nrows, con
         for (int i = 0; i < nrows; ++i) xv -= cs[i] * V[(size_t)i * ldv + e];
         x[e] = xv;
       }
-      const float y = xv * xv - ncomp;
-      const float t = nacc + y;
-      ncomp = (t - nacc) - y;
-      nacc = t;
+      df_fma(nhi, nlo, xv, xv);
     }
     xs[le] = xv;
   }
@@ -189,20 +186,17 @@ __global__ void __launch_bounds__(VCH_THREADS) k_vchunk(size_t n, int nrows, con
   if (mode & VCH_DOTS) {
     for (int i = wid; i < nrows; i += nw) {
       const float* vi = V + (size_t)i * ldv + beg;
-      float acc = 0.f, comp = 0.f;
+      float hi = 0.f, lo = 0.f;
       for (int le = lane; le < CH; le += 32) {
         if (beg + le >= n) break;
-        const float y = vi[le] * xs[le] - comp;
-        const float t = acc + y;
-        comp = (t - acc) - y;
-        acc = t;
+        df_fma(hi, lo, vi[le], xs[le]);
       }
-      const float2 r = warp_df(acc, comp);
+      const float2 r = warp_df_pair(hi, lo);
       if (lane == 0) part[(size_t)i * nch + ch] = r;
     }
   }
   if (mode & VCH_NORM) {
-    const float2 r = warp_df(nacc, ncomp);
+    const float2 r = warp_df_pair(nhi, nlo);
     __shared__ float2 wn[8];
     if (lane == 0) wn[wid] = r;
     __syncthreads();
@@ -257,17 +251,17 @@ __global__ void __launch_bounds__(VCH_THREADS) k_gram_col(int m, int nr, const f
   const int nrows = nr + 1;            // rows V_0..V_{nr-1} and vj itself
   // rows 0..nr: two dots each (slots 2i, 2i+1); row nr+1: atb.vj and dtc.vj
   for (int i = wid; i <= nrows; i += nw) {
-    float a1 = 0.f, c1 = 0.f, a2 = 0.f, c2 = 0.f;
+    float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
     const float* vi = i < nr ? V + (size_t)i * n : vj;
     for (int le = lane; le < CH; le += 32) {
       if (beg + le >= n) break;
       float p1, q1, p2, q2;
       if (i < nrows) { const float vv = vi[beg + le]; p1 = vv; q1 = ts[le]; p2 = vv; q2 = ys[le]; }
       else { const float vv = vj[beg + le]; p1 = with_a ? atb[beg + le] : 0.f; q1 = vv; p2 = dtc ? dtc[beg + le] : 0.f; q2 = vv; }
-      float y = p1 * q1 - c1, tt = a1 + y; c1 = (tt - a1) - y; a1 = tt;
-      y = p2 * q2 - c2; tt = a2 + y; c2 = (tt - a2) - y; a2 = tt;
+      df_fma(h1, l1, p1, q1);
+      df_fma(h2, l2, p2, q2);
     }
-    const float2 r1 = warp_df(a1, c1), r2 = warp_df(a2, c2);
+    const float2 r1 = warp_df_pair(h1, l1), r2 = warp_df_pair(h2, l2);
     if (lane == 0) {
       part[(size_t)(2 * i) * nch + ch] = r1;
       part[(size_t)(2 * i + 1) * nch + ch] = r2;
@@ -275,70 +269,119 @@ __global__ void __launch_bounds__(VCH_THREADS) k_gram_col(int m, int nr, const f
   }
 }
 
-// D part of nb Gram columns at once (the basis is cached, so G_A is known):
-// for the columns j = j0 .. j0+nb-1, with y_j = L^T diag(w^2) L v_j computed
-// here, GD[i*ld + j] = V_i . y_j for i <= j and gD[j] = dtc . v_j (dtc may be
-// null -> 0), as chunk partials in slot i * nb + (j - j0) (row i = j0 + nb is
-// the g_D row), summed by k_part_reduce with RedDcols. Each chunk of V is
-// read once for all nb columns. part needs (j0 + nb + 1) * nb * gridDim.x
-// float2.
-constexpr int GDB_NB = 8;
+// ---- G_D of a whole basis at once ------------------------------------------------
+// G_D = V^T L^T diag(w^2) L V = Z^T Z with Z = diag(w) L V, the 2n x kk matrix
+// of the basis's weighted gradients. One pass over V: each block takes a
+// contiguous pixel range, forms the rows of Z of its pixels (x- and y-plane
+// components) in shared memory, SK_PC pixels at a time, and accumulates
+// Z_rows^T Z_rows in registers: thread t owns the SK_TI x SK_TI output block
+// (bi, bj), bi <= bj, of the upper triangle (FP32 products, FP32 sums over the
+// block's pixel range). The per-block partials are added in double, in block
+// order, by k_gram_dtd_reduce. The result depends only on V, the weights and
+// the pixel ranges, so a cached basis and a rebuilt one give the same G_D.
+constexpr int SK_TI = 11;                          // outputs per thread and dimension
+constexpr int SK_NB = 15;                          // block rows (kk <= 165)
+constexpr int SK_KMAX = SK_TI * SK_NB;
+constexpr int SK_NPAIR = SK_NB * (SK_NB + 1) / 2;  // 120 upper-triangle blocks
+constexpr int SK_THREADS = 128;
+constexpr int SK_PC = 32;                          // pixels per shared-memory stage
+constexpr int SK_SLOTS = SK_NPAIR * SK_TI * SK_TI;
+
+__device__ __forceinline__ void sk_pair(int t, int nb, int& bi, int& bj) {
+  bi = 0;
+  while (t >= nb - bi) { t -= nb - bi; ++bi; }
+  bj = bi + t;
+}
+
+// part[blk * nslot + e * npair + t] = partial of entry e = ii * SK_TI + jj of
+// block pair t, nslot = npair * SK_TI^2, npair = nb (nb + 1) / 2.
 template <typename T>
-__global__ void __launch_bounds__(VCH_THREADS) k_gram_dcols(int m, int j0, int nb, const float* __restrict__ V,
-    const T* __restrict__ wx, const T* __restrict__ wy, const float* __restrict__ dtc, float2* __restrict__ part,
-    int E) {
-  extern __shared__ __align__(16) float ysm[];          // [nb][E * VCH_THREADS]
+__global__ void __launch_bounds__(SK_THREADS) k_gram_dtd(int m, int kk, const float* __restrict__ V,
+    const T* __restrict__ wx, const T* __restrict__ wy, int ppb, float* __restrict__ part) {
+  __shared__ float zs[2 * SK_PC][SK_KMAX];
   const size_t n = (size_t)m * m;
-  const int nch = gridDim.x, ch = blockIdx.x;
-  const int CH = E * VCH_THREADS;
-  const size_t beg = (size_t)ch * CH;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = VCH_THREADS / 32;
-  auto W = [&](const T* p, size_t q) -> float { return p ? (float)to_acc(p[q]) : 1.f; };
-  for (int c = 0; c < nb; ++c) {
-    const float* vj = V + (size_t)(j0 + c) * n;
-    for (int k = 0; k < E; ++k) {
-      const int le = k * VCH_THREADS + tid;
-      const size_t i = beg + le;
-      float yv = 0.f;
-      if (i < n) {
-        const int r = (int)(i % m), cc = (int)(i / m);
+  const int nb = (kk + SK_TI - 1) / SK_TI;
+  const int npair = nb * (nb + 1) / 2;
+  const int kpad = nb * SK_TI;
+  const int t = threadIdx.x;
+  const bool active = t < npair;
+  int bi = 0, bj = 0;
+  if (active) sk_pair(t, nb, bi, bj);
+  float acc[SK_TI][SK_TI];
+#pragma unroll
+  for (int a = 0; a < SK_TI; ++a)
+#pragma unroll
+    for (int b = 0; b < SK_TI; ++b) acc[a][b] = 0.f;
+  const size_t p0 = (size_t)blockIdx.x * ppb;
+  const size_t p1 = (p0 + (size_t)ppb < n) ? p0 + (size_t)ppb : n;
+  for (size_t pc = p0; pc < p1; pc += SK_PC) {
+    __syncthreads();                 // the previous stage's rows are consumed
+    for (int idx = t; idx < SK_PC * kpad; idx += SK_THREADS) {
+      const int r = idx & (SK_PC - 1), j = idx / SK_PC;
+      const size_t i = pc + r;
+      float zx = 0.f, zy = 0.f;
+      if (j < kk && i < p1) {
+        const float* vj = V + (size_t)j * n;
+        const int row = (int)(i % m), col = (int)(i / m);
         const float xv = vj[i];
-        if (r < m - 1) { const float w = W(wx, i); yv -= w * w * (vj[i + 1] - xv); }
-        if (r > 0) { const float w = W(wx, i - 1); yv += w * w * (xv - vj[i - 1]); }
-        if (cc < m - 1) { const float w = W(wy, i); yv -= w * w * (vj[i + m] - xv); }
-        if (cc > 0) { const float w = W(wy, i - m); yv += w * w * (xv - vj[i - m]); }
+        if (row < m - 1) zx = (wx ? (float)to_acc(wx[i]) : 1.f) * (vj[i + 1] - xv);
+        if (col < m - 1) zy = (wy ? (float)to_acc(wy[i]) : 1.f) * (vj[i + m] - xv);
       }
-      ysm[(size_t)c * CH + le] = yv;
+      zs[r][j] = zx;
+      zs[SK_PC + r][j] = zy;
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll 2
+      for (int r = 0; r < 2 * SK_PC; ++r) {
+        float a[SK_TI], b[SK_TI];
+#pragma unroll
+        for (int q = 0; q < SK_TI; ++q) {
+          a[q] = zs[r][bi * SK_TI + q];
+          b[q] = zs[r][bj * SK_TI + q];
+        }
+#pragma unroll
+        for (int x = 0; x < SK_TI; ++x)
+#pragma unroll
+          for (int y = 0; y < SK_TI; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+      }
     }
   }
+  if (active) {
+    const size_t nslot = (size_t)npair * SK_TI * SK_TI;
+    float* out = part + (size_t)blockIdx.x * nslot + t;
+#pragma unroll
+    for (int x = 0; x < SK_TI; ++x)
+#pragma unroll
+      for (int y = 0; y < SK_TI; ++y) out[(size_t)(x * SK_TI + y) * npair] = acc[x][y];
+  }
+}
+
+// GD[i * ld + j] (i <= j < kk) = sum over the nblk block partials, in block
+// order: 32 slots per block of 256 threads, eight groups of blocks summed in
+// parallel and combined in group order.
+__global__ void __launch_bounds__(256) k_gram_dtd_reduce(int nblk, int kk, const float* __restrict__ part,
+                                                         double* __restrict__ GD, int ld) {
+  __shared__ double red[8][32];
+  const int nb = (kk + SK_TI - 1) / SK_TI;
+  const int npair = nb * (nb + 1) / 2;
+  const int nslot = npair * SK_TI * SK_TI;
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int s = blockIdx.x * 32 + lane;
+  double acc = 0.0;
+  if (s < nslot)
+    for (int c = g; c < nblk; c += 8) acc += (double)__ldg(part + (size_t)c * nslot + s);
+  red[g][lane] = acc;
   __syncthreads();
-  const int j1 = j0 + nb;               // rows 0 .. j1-1, then the g_D row
-  for (int i = wid; i <= j1; i += nw) {
-    float a[GDB_NB], cmp[GDB_NB];
+  if (g == 0 && s < nslot) {
+    double tot = 0.0;
 #pragma unroll
-    for (int c = 0; c < GDB_NB; ++c) { a[c] = 0.f; cmp[c] = 0.f; }
-    const bool grow = (i == j1);
-    const float* vi = grow ? dtc : V + (size_t)i * n;
-    if (!(grow && !dtc)) {
-      for (int le = lane; le < CH; le += 32) {
-        if (beg + le >= n) break;
-        const float vv = vi[beg + le];
-#pragma unroll
-        for (int c = 0; c < GDB_NB; ++c) {
-          if (c >= nb) break;
-          const float q = grow ? V[(size_t)(j0 + c) * n + beg + le] : ysm[(size_t)c * CH + le];
-          const float y = vv * q - cmp[c], t = a[c] + y;
-          cmp[c] = (t - a[c]) - y;
-          a[c] = t;
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < GDB_NB; ++c) {
-      if (c >= nb) break;
-      const float2 r = warp_df(a[c], cmp[c]);
-      if (lane == 0) part[((size_t)i * nb + c) * nch + ch] = r;
-    }
+    for (int k = 0; k < 8; ++k) tot += red[k][lane];
+    const int e = s / npair, tp = s - e * npair;
+    int bi, bj;
+    sk_pair(tp, nb, bi, bj);
+    const int i = bi * SK_TI + e / SK_TI, j = bj * SK_TI + e % SK_TI;
+    if (i <= j && j < kk) GD[(size_t)i * ld + j] = tot;
   }
 }
 
@@ -396,18 +439,6 @@ struct RedGramCol {
       return (a_part ? GA : GD) + (size_t)row * ld + jout;
     }
     return (a_part ? gA : gD) + jout;
-  }
-};
-
-// k_gram_dcols slots (see there); the lower triangle is not stored
-struct RedDcols {
-  int j0, nb, ld;
-  double *GD, *gD;
-  __device__ double* dst(int s) const {
-    const int i = s / nb, j = j0 + (s - i * nb);
-    const int j1 = j0 + nb;
-    if (i < j1) return i > j ? nullptr : GD + (size_t)i * ld + j;
-    return gD + j;
   }
 };
 

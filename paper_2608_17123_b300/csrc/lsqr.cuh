@@ -22,14 +22,16 @@ namespace db {
 
 template <typename T, typename Acc>
 struct LsqrProb {
+  using X = typename Traits<T>::X;
   BandOp<Acc> op;
   int m, solver;                 // 0 IRLS (weighted D), 1 MM (c = a0), 2 SB (c = a0 - a1)
   double gamma;
   Acc sg;                        // sqrt(gamma) in working precision
   const T* b;
-  const T* x0;                   // null: start from zero
+  const X* x0;                   // null: start from zero
   const T *a0x, *a0y, *a1x, *a1y;
-  T *uA, *uLx, *uLy, *v, *w, *dlt;
+  T *uA, *uLx, *uLy, *v, *w;
+  X* dlt;
   int tile_begin, ntiles, nt;    // tiles [tile_begin, tile_begin + ntiles), nt per side
 };
 
@@ -80,7 +82,25 @@ __device__ __forceinline__ LsqrState load_state(const LsqrState* s) {
   return r;
 }
 
+// The three per-thread sums of squares of a pass. For float working
+// precision each sum is a double-float pair and each square enters exactly
+// (its rounding error recovered with one FMA), so the tile partials carry
+// about twice float precision; for double working precision, plain doubles.
+template <typename Acc> struct Sums3;
+template <> struct Sums3<float> {
+  float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+  __device__ __forceinline__ void sq(int k, float a) { df_fma(h[k], l[k], a, a); }
+};
+template <> struct Sums3<double> {
+  double h[3] = {0.0, 0.0, 0.0};
+  __device__ __forceinline__ void sq(int k, double a) { h[k] = fma(a, a, h[k]); }
+};
+
 __device__ int lsqr_wait_release(const LsqrCtl& ctl, int ph);
+
+// The waits read the clock every 64 spins, or on every spin when the limit is
+// below 100 us (so that a short limit is honoured).
+__device__ __forceinline__ unsigned spin_mask(const LsqrCtl& ctl) { return ctl.limit_ns < 100000ull ? 0u : 63u; }
 
 // Loads of one tile issued before any of them is used: the problem's done
 // flag and coefficients, the pointwise operands of this thread's pixels, the
@@ -110,14 +130,15 @@ __device__ __forceinline__ TileHead<Acc> load_head(const LsqrCtl& ctl, int p) {
 // Returns false (nothing written) when the problem has already stopped.
 template <typename T, typename Acc>
 __device__ int lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p, bool init, bool first,
-                           int r0, int c0, Acc* sm, Acc (&red)[3], Acc* cbr, Acc* cbc, int ph, bool wait_rel) {
+                           int r0, int c0, Acc* sm, Sums3<Acc>& red, Acc* cbr, Acc* cbc, int ph, bool wait_rel) {
   const int m = P.m;
   const TileGeom g = tile_geom(P.op, false);
   Acc* sx = sm;
   Acc* sz = sx + g.H * g.H;
   Acc* sbr = sz + g.H * TM;
   Acc* sbc = sbr + TM * band_pitch(g.w);
-  const T* src = init ? P.x0 : P.v;
+  using X = typename Traits<T>::X;
+  const bool src = init ? (P.x0 != nullptr) : true;   // input vector: x0 (phase 0) or v
   const bool wtd = (P.solver == 0);
   Acc pu[PIX], px[PIX], py[PIX], pw_[PIX], pd[PIX], wx[PIX], wy[PIX];
   {
@@ -133,14 +154,15 @@ __device__ int lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p,
           pu[j] = ldcg<T>(P.uA + i);
           px[j] = ldcg<T>(P.uLx + i);
           py[j] = ldcg<T>(P.uLy + i);
-          if (!first) { pw_[j] = ldcg<T>(P.w + i); pd[j] = ldcg<T>(P.dlt + i); }
+          if (!first) { pw_[j] = ldcg<T>(P.w + i); pd[j] = ldcg<X>(P.dlt + i); }
         }
         if (wtd) { wx[j] = to_acc(P.a0x[i]); wy[j] = to_acc(P.a0y[i]); }
       }
     }
   }
   if (src) {
-    gather_tile<true, T, Acc>(src, m, r0, c0, g, Acc(1), sx);
+    if (init) gather_tile<true, X, Acc>(P.x0, m, r0, c0, g, Acc(1), sx);
+    else gather_tile<true, T, Acc>(P.v, m, r0, c0, g, Acc(1), sx);
     if (!cbr) load_bands<Acc>(P.op, false, 0, r0, c0, g, sbr, sbc);
   }
   Acc Av[PIX] = {};
@@ -159,7 +181,6 @@ __device__ int lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p,
   const Acc phr = h.K.phr, thr = h.K.thr;
   const int r = r0 + threadIdx.x;
   const int lr = threadIdx.x - g.lo;
-  Acc s_u = 0, s_d = 0, s_w = 0;
 #pragma unroll
   for (int j = 0; j < PIX; ++j) {
     const int cl = pix_col(j);
@@ -185,7 +206,7 @@ __device__ int lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p,
       ua = to_acc(P.b[i]) - av;
       ux = sg * (cx - qx);
       uy = sg * (cy - qy);
-      P.dlt[i] = store_cast<T, Acc>(Acc(0));
+      P.dlt[i] = store_cast<X, Acc>(Acc(0));
     } else {
       ua = av - ab * pu[j];
       ux = sg * qx - ab * px[j];
@@ -195,10 +216,10 @@ __device__ int lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p,
       } else {
         const Acc wo = pw_[j];
         const Acc dn = pd[j] + phr * wo;
-        P.dlt[i] = store_cast<T, Acc>(dn);
+        P.dlt[i] = store_cast<X, Acc>(dn);
         P.w[i] = store_cast<T, Acc>(v0 - thr * wo);
-        s_d += dn * dn;
-        s_w += wo * wo;
+        red.sq(1, dn);
+        red.sq(2, wo);
       }
     }
     if (r == m - 1) ux = 0;
@@ -206,17 +227,16 @@ __device__ int lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p,
     P.uA[i] = store_cast<T, Acc>(ua);
     P.uLx[i] = store_cast<T, Acc>(ux);
     P.uLy[i] = store_cast<T, Acc>(uy);
-    s_u += ua * ua + ux * ux + uy * uy;
+    red.sq(0, ua);
+    red.sq(0, ux);
+    red.sq(0, uy);
   }
-  red[0] = s_u;
-  red[1] = s_d;
-  red[2] = s_w;
   return 1;
 }
 
 template <typename T, typename Acc>
 __device__ int lsqr_pass_B(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p, bool init,
-                           int r0, int c0, Acc* sm, Acc (&red)[3], Acc* cbr, Acc* cbc, int ph, bool wait_rel) {
+                           int r0, int c0, Acc* sm, Sums3<Acc>& red, Acc* cbr, Acc* cbc, int ph, bool wait_rel) {
   const int m = P.m;
   const TileGeom g = tile_geom(P.op, true);
   Acc* sx = sm;
@@ -265,7 +285,6 @@ __device__ int lsqr_pass_B(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p,
   const Acc sgb = P.sg * ib;
   const Acc ba = init ? Acc(0) : h.K.ba;
   const int r = r0 + threadIdx.x;
-  Acc s_v = 0;
 #pragma unroll
   for (int j = 0; j < PIX; ++j) {
     const int c = c0 + pix_col(j);
@@ -274,11 +293,8 @@ __device__ int lsqr_pass_B(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p,
     Acc vt = ib * At[j] + sgb * lt[j];
     if (!init) vt -= ba * vo[j];
     P.v[i] = store_cast<T, Acc>(vt);
-    s_v += vt * vt;
+    red.sq(0, vt);
   }
-  red[0] = s_v;
-  red[1] = Acc(0);
-  red[2] = Acc(0);
   return 1;
 }
 
@@ -368,12 +384,12 @@ __device__ __forceinline__ int lsqr_finish_B(LsqrState S, LsqrState* st, LsqrCoe
 // them, stored as (hi, lo) float pairs -- no FP64 instruction, whose issue
 // costs ~64 cycles per warp instruction on this part. Double working
 // precision: FP64 block sum, stored as doubles.
-__device__ __forceinline__ void tile_partial(const float (&red)[3], double* part_tile, double* scratch) {
+__device__ __forceinline__ void tile_partial(const Sums3<float>& red, double* part_tile, double* scratch) {
   const int tid = threadIdx.x + 32 * threadIdx.y, lane = tid & 31, wid = tid >> 5;
   float2* sw = reinterpret_cast<float2*>(scratch);          // [3][8]
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const float2 r = warp_df(red[k], 0.f);
+    const float2 r = warp_df_pair(red.h[k], red.l[k]);
     if (lane == 0) sw[k * 8 + wid] = r;
   }
   __syncthreads();
@@ -391,9 +407,9 @@ __device__ __forceinline__ void tile_partial(const float (&red)[3], double* part
     }
   }
 }
-__device__ __forceinline__ void tile_partial(const double (&red)[3], double* part_tile, double* scratch) {
+__device__ __forceinline__ void tile_partial(const Sums3<double>& red, double* part_tile, double* scratch) {
   double tot[3];
-  block_sum_to0<3, double>(red, tot, scratch);
+  block_sum_to0<3, double>(red.h, tot, scratch);
   if (threadIdx.x == 0 && threadIdx.y == 0) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) part_tile[k] = tot[k];
@@ -514,7 +530,7 @@ __device__ int lsqr_phase_arrive(const LsqrProb<T, Acc>* probs, const LsqrCtl& c
     unsigned spins = 0;
     while (aref(gb->count).load(cuda::memory_order_acquire) < target) {
       if (*(volatile int*)&gb->error) { s_ok = 0; break; }
-      if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > ctl.limit_ns) {
+      if (((++spins) & spin_mask(ctl)) == 0 && globaltimer_ns() - t0 > ctl.limit_ns) {
         atomicExch(&gb->error, 1);
         s_ok = 0;
         break;
@@ -538,7 +554,7 @@ __device__ int lsqr_wait_release(const LsqrCtl& ctl, int ph) {
     int res = 0;
     while (aref(gb->gen).load(cuda::memory_order_acquire) < (unsigned)ph) {
       if (*(volatile int*)&gb->error) { res = -1; break; }
-      if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > ctl.limit_ns) {
+      if (((++spins) & spin_mask(ctl)) == 0 && globaltimer_ns() - t0 > ctl.limit_ns) {
         atomicExch(&gb->error, 1);
         res = -1;
         break;
@@ -604,7 +620,7 @@ __global__ void __launch_bounds__(256, 2) k_lsqr(const LsqrProb<T, Acc>* __restr
         const LsqrProb<T, Acc>& P = cached ? s_prob[k] : probs[p];
         const int tl = tile - P.tile_begin;
         const int r0 = (tl % P.nt) * TM, c0 = (tl / P.nt) * TN;
-        Acc red[3];
+        Sums3<Acc> red;
         __syncthreads();   // shared memory of the previous tile is free
         Acc* cbr = nullptr;
         Acc* cbc = nullptr;

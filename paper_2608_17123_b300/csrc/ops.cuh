@@ -153,8 +153,9 @@ __device__ __forceinline__ void load_bands(const BandOp<Acc>& op, bool tr, int t
   }
 }
 
-// The two 1-D passes of one separable term. KW > 0: bands at most KW wide,
-// loops fully unrolled (every shared-memory load of an output issued before
+// The two 1-D passes of one separable term. KW > 0: bands at most KW wide
+// (KW = 16, or 32 in float working precision, where the taps fit the
+// register budget), loops fully unrolled (every shared-memory load of an output issued before
 // its FMAs, taps of step 1 held in registers, two partial sums); KW == 0:
 // any width, runtime loop.
 template <int KW, typename Acc>
@@ -240,6 +241,7 @@ __device__ __forceinline__ void tile_conv(const BandOp<Acc>& op, bool tr, int r0
     }
     __syncthreads();
     if (g.w <= 16) conv_term<16, Acc>(g, sx, sz, sbr, sbc, out);
+    else if (sizeof(Acc) == 4 && g.w <= 32) conv_term<sizeof(Acc) == 4 ? 32 : 0, Acc>(g, sx, sz, sbr, sbc, out);
     else conv_term<0, Acc>(g, sx, sz, sbr, sbc, out);
   }
 }

@@ -27,8 +27,8 @@ enum AuxMode { AUX_APPROACH_I = 0, AUX_FROM_X = 1 };
 
 // Initial auxiliaries of a level (Sec. 4.1).
 template <typename T>
-__global__ void k_aux_init(int m, int solver, int mode, const T* __restrict__ x, T* a0x, T* a0y,
-                           T* a1x, T* a1y, double eps_irls, double eps_mm, double tau) {
+__global__ void k_aux_init(int m, int solver, int mode, const typename Traits<T>::X* __restrict__ x, T* a0x,
+                           T* a0y, T* a1x, T* a1y, double eps_irls, double eps_mm, double tau) {
   using Acc = typename Traits<T>::Acc;
   size_t n = (size_t)m * m;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -64,10 +64,12 @@ __global__ void k_aux_init(int m, int solver, int mode, const T* __restrict__ x,
 // by the last block into out[0..1]. solver < 0 skips the auxiliary update.
 template <typename T>
 __global__ void __launch_bounds__(256) k_outer_update(int m, int solver, int warm,
-    const T* __restrict__ x_old, const T* __restrict__ dlt, T* __restrict__ x_new,
+    const typename Traits<T>::X* __restrict__ x_old, const typename Traits<T>::X* __restrict__ dlt,
+    typename Traits<T>::X* __restrict__ x_new,
     T* a0x, T* a0y, T* a1x, T* a1y, double eps_irls, double eps_mm, double tau,
     double* part, unsigned* cnt, double* out) {
   using Acc = typename Traits<T>::Acc;
+  using X = typename Traits<T>::X;
   __shared__ double scratch[2 * 32];
   __shared__ int s_flag;
   size_t n = (size_t)m * m;
@@ -80,7 +82,7 @@ __global__ void __launch_bounds__(256) k_outer_update(int m, int solver, int war
     };
     const Acc xo = to_acc(x_old[i]);
     const Acc xn = xn_at(i);
-    x_new[i] = store_cast<T, Acc>(xn);
+    x_new[i] = store_cast<X, Acc>(xn);
     const Acc dx = xn - xo;
     s0 += dx * dx;
     s1 += xo * xo;

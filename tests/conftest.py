@@ -11,3 +11,8 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (B300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running oracle case")
+
+
+def pytest_sessionfinish(session, exitstatus):
+    from parity import write_report
+    write_report()

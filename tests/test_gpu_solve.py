@@ -1,15 +1,15 @@
 """End-to-end V-cycle solves (Alg. 4 with Alg. 1-3) on the GPU against the
 FP64 oracle: reconstruction, per-level outer iteration counts and gamma.
 
-The method is sensitive to rounding-level perturbations (LSQR without
-reorthogonalisation stopped at its iteration limit, GCV on small coarse
-levels), so the oracle rerun with unit-roundoff noise of the storage
-precision injected into every operator output (tests/perturb.py) already
-differs from the plain oracle run. The spread is the largest distance from
-the plain run over two such reruns with independent noise (one rerun alone
-under-estimates it on the chaotic IRLS cycles). Each tolerance is the larger
-of the stated target (x: 1e-4 FP32, 1e-6 FP64; gamma: 1 %; outer
-iterations: +-1) and ten times that measured spread.
+Tolerances follow tests/parity.py: the stated targets (x: 1e-4 FP32, 1e-6
+FP64; gamma: 1 %; outer iterations: +-1), except where the oracle's own
+result is not determined to that precision -- its spread over three reruns
+with unit-roundoff noise of the storage precision injected into every
+operator output exceeds the target -- and the GPU result must then land
+within twice that spread. On these small levels that is common: the GCV
+minimiser is located only to Brent's tolerance, the doubling of the
+projected dimension stops on a 0.1 % test, and coarse levels that run to
+K_max carry every perturbation to the end.
 """
 import numpy as np
 import pytest
@@ -20,12 +20,14 @@ from paper_2608_17123_b300 import api
 from paper_2608_17123_b300 import inputs as I
 
 from helpers import rel
+from parity import check_solve
 from perturb import noisy
 
 pytestmark = pytest.mark.gpu
 
 _CACHE = {}
 XTOL = {"fp64": 1e-6, "fp32": 1e-4}
+PERTURB_SEEDS = (12345, 777, 4242)
 
 
 def case(m, sigma, Sz, nr, nd, seed, noise):
@@ -39,29 +41,20 @@ def case(m, sigma, Sz, nr, nd, seed, noise):
     return _CACHE[key]
 
 
+def storage_rounded(b, prec):
+    """The input as the GPU stores it: FP32 storage rounds b to float32, so
+    the oracle is given the same rounded values."""
+    return b.astype(np.float32).astype(np.float64) if prec == "fp32" else b
+
+
 def references(A, b, combo, prec):
+    b = storage_rounded(b, prec)
     key = ("ref", id(A), combo, prec)
     if key not in _CACHE:
         r0 = S.mgm(b, A, *combo)
-        r1 = [noisy(lambda: S.mgm(b, A, *combo), prec, seed) for seed in (12345, 777)]
+        r1 = [noisy(lambda: S.mgm(b, A, *combo), prec, seed) for seed in PERTURB_SEEDS]
         _CACHE[key] = (r0, r1)
     return _CACHE[key]
-
-
-def compare(r, r0, r1, prec):
-    """r1: the perturbed oracle reruns (a list, or one result)."""
-    runs = r1 if isinstance(r1, list) else [r1]
-    spread_x = max(rel(q["x"], r0["x"]) for q in runs)
-    d = rel(r["x"], r0["x"])
-    assert d <= max(XTOL[prec], 10 * spread_x), f"x rel diff {d:.2e} (oracle spread {spread_x:.2e})"
-    for i in range(len(r0["iters"])):
-        spread_it = max(abs(q["iters"][i] - r0["iters"][i]) for q in runs)
-        assert abs(r["iters"][i] - r0["iters"][i]) <= max(1, 2 * spread_it), \
-            (i, r["iters"], r0["iters"], [q["iters"] for q in runs])
-        spread_mu = max(abs(q["mu"][i] - r0["mu"][i]) for q in runs) / r0["mu"][i]
-        dm = abs(r["mu"][i] - r0["mu"][i]) / r0["mu"][i]
-        assert dm <= max(1e-2, 10 * spread_mu), (i, r["mu"], r0["mu"], [q["mu"] for q in runs])
-    return d, spread_x
 
 
 COMBOS = [("irls", "haar", 1, "X"), ("irls", "haar", 2, "X"), ("irls", "db4", 3, "D"),
@@ -74,8 +67,8 @@ COMBOS = [("irls", "haar", 1, "X"), ("irls", "haar", 2, "X"), ("irls", "db4", 3,
 def test_solve_matches_oracle_m32(prec, combo):
     A, b, _, psf = case(32, 1.5, 7, 6, 3, 1, 0.01)
     r0, r1 = references(A, b, combo, prec)
-    r = api.deblur_solve(b, psf, *combo, precision=prec)
-    compare(r, r0, r1, prec)
+    r = api.deblur_solve(storage_rounded(b, prec), psf, *combo, precision=prec)
+    check_solve(f"solve_m32[{prec}-{'-'.join(map(str, combo))}]", r, r0, r1, XTOL[prec], rel)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -84,8 +77,8 @@ def test_solve_config_m64_irls(prec):
     transferring the solution."""
     A, b, x_true, psf = case(64, 2.0, 9, 12, 6, 0, 0.01)
     r0, r1 = references(A, b, ("irls", "haar", 2, "X"), prec)
-    r = api.deblur_solve(b, psf, "irls", "haar", 2, "X", precision=prec)
-    compare(r, r0, r1, prec)
+    r = api.deblur_solve(storage_rounded(b, prec), psf, "irls", "haar", 2, "X", precision=prec)
+    check_solve(f"solve_m64_irls[{prec}]", r, r0, r1, XTOL[prec], rel)
     assert rel(r["x"], x_true) < 0.3
 
 
