@@ -664,6 +664,189 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------------------ batched / served workloads
+def uneven_requests(count, sizes, seed, noise_range=(0.01, 0.01)):
+    """`count` requests of uneven size: m uniform over `sizes`, Gaussian PSF
+    sigma ~ U[1.5, 6] on S = min(31, 2 ceil(3 sigma) + 1), noise level
+    uniform over noise_range, solver / wavelet / transfer each uniform,
+    3-level cycles (up to log2(m) - 6 levels for m < 512), phantoms with
+    40 sqrt(m / 512) rectangles and half as many disks. Returns a list of
+    dicts (b without noise rounding: the FP32 path rounds on the device)."""
+    from paper_2608_17123_b300 import inputs as I
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for k in range(count):
+        m = int(rng.choice(sizes))
+        sigma = float(rng.uniform(1.5, 6.0))
+        S_ = min(31, 2 * int(math.ceil(3 * sigma)) + 1)
+        solver = ("irls", "mm", "sb")[int(rng.integers(3))]
+        wavelet = ("haar", "db4")[int(rng.integers(2))]
+        transfer = ("X", "D")[int(rng.integers(2))]
+        noise = float(rng.uniform(*noise_range))
+        R = max(4, int(round(40 * math.sqrt(m / 512))))
+        reqs.append(dict(m=m, sigma=sigma, S=S_, solver=solver, wavelet=wavelet, transfer=transfer,
+                         noise=noise, levels=3, seed=1000 + k, nr=R, nd=R // 2))
+    return reqs
+
+
+def materialise(api, torch, reqs):
+    from paper_2608_17123_b300 import inputs as I
+    out = []
+    for r in reqs:
+        psf = I.gaussian_psf(r["sigma"], r["S"])
+        x_true = I.phantom(r["m"], r["nr"], r["nd"], r["seed"])
+        b = make_b(api, torch, r["m"], x_true, psf, r["noise"], 30_000 + r["seed"])
+        out.append(dict(b=b, psf=psf, solver=r["solver"], wavelet=r["wavelet"], levels=r["levels"],
+                        transfer=r["transfer"], x_true=x_true))
+    return out
+
+
+def run_batch_workload(args):
+    """64 images of uneven size (m in {128, 256, 512, 1024, 2048}, seed 7),
+    mixed PSFs, solvers, wavelets and transfers, FP32: one deblur_solve_batch
+    call against the same 64 solves one at a time (deblur_solve), images/s
+    of each and the largest difference between the two reconstructions."""
+    import torch
+    from paper_2608_17123_b300 import api
+    reqs = materialise(api, torch, uneven_requests(args.batch_images, (128, 256, 512, 1024, 2048), 7))
+    ctx = api.Context(0)
+    api.deblur_solve(reqs[0]["b"], reqs[0]["psf"], reqs[0]["solver"], reqs[0]["wavelet"], 3, reqs[0]["transfer"],
+                     precision="fp32", ctx=ctx)   # warm-up (module load, first launches)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [api.deblur_solve(r["b"], r["psf"], r["solver"], r["wavelet"], 3, r["transfer"], precision="fp32",
+                              ctx=ctx) for r in reqs]
+    t_plain = time.perf_counter() - t0
+    probs = [{k: r[k] for k in ("b", "psf", "solver", "wavelet", "levels", "transfer")} for r in reqs]
+    t0 = time.perf_counter()
+    batched = api.deblur_solve_batch(probs, precision="fp32", ctx=ctx)
+    t_batch = time.perf_counter() - t0
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    pix = sum(r["b"].size for r in reqs)
+    n = len(reqs)
+    return {"workload": "batch64_uneven_m128-2048_mixed", "images": n, "megapixels": round(pix / 1e6, 3),
+            "sizes": sorted(set(r["b"].shape[0] for r in reqs)),
+            "plain": {"images_per_s": round(n / t_plain, 4), "mpixel_per_s": round(pix / t_plain / 1e6, 4),
+                      "s": round(t_plain, 2)},
+            "batched": {"images_per_s": round(n / t_batch, 4), "mpixel_per_s": round(pix / t_batch / 1e6, 4),
+                        "s": round(t_batch, 2)},
+            "speedup": round(t_plain / t_batch, 3),
+            "max_rel_diff_batched_vs_plain": max(rel(b["x"], p["x"]) for b, p in zip(batched, plain)),
+            "io": "host buffers (each call copies its inputs in and its result out)", "precision": "fp32"}
+
+
+def run_serve_workload(args):
+    """Continuous-batching server under a Poisson request stream: requests of
+    m in {256, 512, 1024} (mixed PSFs, solvers, wavelets, transfers, noise
+    1-5 %), the rate swept over fractions of the plain one-at-a-time
+    throughput of the same requests; images/s delivered and p50/p99 latency
+    (arrival to completion) at each rate, and the largest difference of a
+    served result from its one-at-a-time solve."""
+    import torch
+    from paper_2608_17123_b300 import api
+    reqs = materialise(api, torch, uneven_requests(args.serve_requests, (256, 512, 1024), 11, (0.01, 0.05)))
+    ctx = api.Context(0)
+    api.deblur_solve(reqs[0]["b"], reqs[0]["psf"], reqs[0]["solver"], reqs[0]["wavelet"], 3, reqs[0]["transfer"],
+                     precision="fp32", ctx=ctx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [api.deblur_solve(r["b"], r["psf"], r["solver"], r["wavelet"], 3, r["transfer"], precision="fp32",
+                              ctx=ctx) for r in reqs]
+    t_plain = time.perf_counter() - t0
+    plain_rate = len(reqs) / t_plain
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    points = []
+    worst = 0.0
+    for frac in args.serve_rates:
+        rate = frac * plain_rate
+        rng = np.random.default_rng(int(1000 * frac))
+        gaps = rng.exponential(1.0 / rate, size=len(reqs))
+        srv = api.Server(max_resident=args.serve_slots, max_m=1024, ctx=ctx)
+        t0 = time.perf_counter()
+        tks, t_next = [], 0.0
+        for k, r in enumerate(reqs):
+            t_next += gaps[k]
+            while time.perf_counter() - t0 < t_next:
+                time.sleep(0.0005)
+            tks.append(srv.submit(r["b"], r["psf"], r["solver"], r["wavelet"], 3, r["transfer"]))
+        res = [srv.poll(t) for t in tks]
+        t_all = time.perf_counter() - t0
+        srv.close()
+        lat = [l for _, l in res]
+        worst = max(worst, max(rel(q["x"], p["x"]) for (q, _), p in zip(res, plain)))
+        points.append({"offered_fraction_of_plain": frac, "offered_per_s": round(rate, 3),
+                       "delivered_images_per_s": round(len(reqs) / t_all, 4),
+                       "p50_ms": round(float(np.percentile(lat, 50)), 1),
+                       "p99_ms": round(float(np.percentile(lat, 99)), 1)})
+    return {"workload": "serve_poisson_m256-1024_mixed", "requests_per_point": len(reqs),
+            "slots": args.serve_slots, "plain_images_per_s": round(plain_rate, 4),
+            "plain_p50_ms": round(1e3 * t_plain / len(reqs), 1), "points": points,
+            "max_rel_diff_served_vs_plain": worst, "precision": "fp32"}
+
+
+# ------------------------------------------------------------------ phantom study
+def ssim(x, y, L=None, win=11, sigma=1.5):
+    """Structural similarity index (Wang, Bovik, Sheikh, Simoncelli 2004):
+    local means, variances and covariance over Gaussian-weighted win x win
+    windows (standard deviation sigma, weights summing to 1), the index
+    ((2 mu_x mu_y + c1)(2 s_xy + c2)) / ((mu_x^2 + mu_y^2 + c1)(s_x^2 + s_y^2 + c2))
+    with c1 = (0.01 L)^2, c2 = (0.03 L)^2, averaged over every window that
+    lies inside the image. L: dynamic range (default: that of x)."""
+    from scipy.signal import convolve2d
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    if L is None:
+        L = float(x.max() - x.min()) or 1.0
+    r = win // 2
+    g = np.exp(-(np.arange(-r, r + 1) ** 2) / (2.0 * sigma * sigma))
+    w = np.outer(g, g)
+    w /= w.sum()
+    f = lambda a: convolve2d(a, w, mode="valid")
+    mx, my = f(x), f(y)
+    sxx = f(x * x) - mx * mx
+    syy = f(y * y) - my * my
+    sxy = f(x * y) - mx * my
+    c1, c2 = (0.01 * L) ** 2, (0.03 * L) ** 2
+    smap = ((2 * mx * my + c1) * (2 * sxy + c2)) / ((mx * mx + my * my + c1) * (sxx + syy + c2))
+    return float(smap.mean())
+
+
+def run_phantom_study(args):
+    """The paper's experiments (Sec. 5) on synthetic phantoms: 64 x 64
+    two-level and 128 x 128 three-level V-cycles, Gaussian blur sigma = 3.5
+    and 4.5, 1 % noise; IRLS, MM and SB, each single-level (Approach I, at
+    64 x 64) and with HWT-D, HWT-X, DWT-D, DWT-X. Reports RRE, SSIM, device
+    time and outer iterations per level for every run."""
+    import torch
+    from paper_2608_17123_b300 import api
+    from paper_2608_17123_b300 import inputs as I
+    ctx = api.Context(0)
+    rows = []
+    for m, levels, nr, nd in ((64, 2, 12, 6), (128, 3, 24, 12)):
+        x_true = I.phantom(m, nr, nd, SEED)
+        for sigma in (3.5, 4.5):
+            S_ = 2 * int(math.ceil(3 * sigma)) + 1
+            psf = I.gaussian_psf(sigma, S_)
+            b = make_b(api, torch, m, x_true, psf, 0.01, 20_000 + m)
+            runs = [("I", "haar", 1)] if levels == 2 else []
+            runs += [(t, w, levels) for w in ("haar", "db4") for t in ("D", "X")]
+            for solver in ("irls", "mm", "sb"):
+                for transfer, wavelet, lv in runs:
+                    api.deblur_solve(b, psf, solver, wavelet, lv, transfer, precision="fp64", ctx=ctx)  # warm
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    r = api.deblur_solve(b, psf, solver, wavelet, lv, transfer, precision="fp64", ctx=ctx)
+                    dt = time.perf_counter() - t0
+                    name = "I" if lv == 1 else ("HWT" if wavelet == "haar" else "DWT") + "-" + transfer
+                    rows.append({"m": m, "sigma": sigma, "solver": solver, "method": name,
+                                 "rre": round(float(np.linalg.norm(r["x"] - x_true) / np.linalg.norm(x_true)), 4),
+                                 "ssim": round(ssim(x_true, r["x"]), 4), "ms": round(dt * 1e3, 1),
+                                 "iters": r["iters"]})
+    ctx.close()
+    return {"study": "phantom_multilevel", "precision": "fp64", "psf": "gaussian, S = 2 ceil(3 sigma) + 1",
+            "noise": "1%", "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -675,7 +858,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", dest="forms", action="store_false",
                     help="skip the batched / serving comparison")
+    ap.add_argument("--workload", default="m512", choices=["m512", "batch", "serve", "study"],
+                    help="m512: the benchmark line; batch: 64 uneven images batched vs one at a time; "
+                         "serve: Poisson request stream against the server; study: the phantom study of "
+                         "the paper's experiments")
+    ap.add_argument("--batch-images", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 1.0, 2.0, 4.0])
     args = ap.parse_args()
+    if args.workload != "m512":
+        fn = {"batch": run_batch_workload, "serve": run_serve_workload, "study": run_phantom_study}[args.workload]
+        print(json.dumps(fn(args)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and args.impl == "ours":

@@ -1241,13 +1241,15 @@ struct BatchSolver {
     X* xn = nullptr;
     std::vector<double> mu;
     std::vector<int> iters, inners;
+    // GCV workspace of this problem: its Krylov basis stays cached across
+    // the outer iterations of a level, as in a single solve
+    GcvBufs<Acc> gb;
   };
   db_context* ctx;
   cudaStream_t st;
   db_opts o;
   db_gcv_opts go;
   std::vector<Prob> P;
-  std::vector<GcvBufs<Acc>> gbufs;
   std::vector<cudaStream_t> wst;
   LsqrProb<T, Acc>* d_probs = nullptr;
   LsqrState* d_states = nullptr;
@@ -1264,27 +1266,29 @@ struct BatchSolver {
     for (auto w : wst) cudaStreamDestroy(w);
   }
 
-  static int workers_for(int count) { return std::max(1, std::min(count, 4)); }
+  static int workers_for(int count) { return std::max(1, std::min(count, 8)); }
 
-  static size_t footprint(int count, const db_request* r, const db_gcv_opts& g) {
-    size_t tot = 0, n0max = 0, tiles = 0;
+  // device bytes of one problem: its levels and its GCV workspace
+  static size_t problem_bytes(int m, int levels, int psf_size, const db_gcv_opts& g, int nsm) {
+    return Engine<T>::footprint_levels(m, levels, psf_size) + (4ull << 20) +
+           GcvBufs<Acc>::bytes((size_t)m * m, Engine<T>::gram_dim(g), g.exact_max_pixels, nsm);
+  }
+
+  static size_t footprint(int count, const db_request* r, const db_gcv_opts& g, int nsm) {
+    size_t tot = 0, tiles = 0;
     for (int i = 0; i < count; ++i) {
-      tot += Engine<T>::footprint_levels(r[i].m, r[i].levels, r[i].psf_size) + (4ull << 20);
-      n0max = std::max(n0max, (size_t)r[i].m * r[i].m);
+      tot += problem_bytes(r[i].m, r[i].levels, r[i].psf_size, g, nsm);
       tiles += (size_t)((r[i].m + TM - 1) / TM) * ((r[i].m + TM - 1) / TM);
     }
-    tot += (size_t)workers_for(count) * GcvBufs<Acc>::bytes(n0max, Engine<T>::gram_dim(g), g.exact_max_pixels, 160);
     tot += (size_t)count * (sizeof(LsqrProb<T, Acc>) + sizeof(LsqrState) + sizeof(LsqrCoef<Acc>) + 4 * 256 + 64);
     tot += tiles * (6 * sizeof(double) + sizeof(int)) + (16ull << 20);
     return tot;
   }
 
   // Shared buffers: batched-LSQR tables for up to max_probs problems and
-  // max_tiles tiles, and the GCV workspaces of the worker streams.
-  void alloc_shared(Arena& A, int max_probs, size_t tiles, size_t n0max, int nworkers) {
+  // max_tiles tiles, and the worker streams of the GCV evaluations.
+  void alloc_shared(Arena& A, int max_probs, size_t tiles, int nworkers) {
     max_tiles = tiles;
-    gbufs.resize(nworkers);
-    for (int w = 0; w < nworkers; ++w) gbufs[w].alloc(A, n0max, Engine<T>::gram_dim(go), go.exact_max_pixels, ctx->nsm);
     wst.resize(nworkers);
     for (int w = 0; w < nworkers; ++w) CK(cudaStreamCreateWithFlags(&wst[w], cudaStreamNonBlocking));
     d_probs = A.take<LsqrProb<T, Acc>>(max_probs);
@@ -1310,6 +1314,7 @@ struct BatchSolver {
     q.levels = r.levels;
     q.tr = q.levels == 1 ? DB_APPROACH_I : r.transfer;
     q.E->build(psf_dev, r.psf_size, r.m, q.levels, q.wv, b_dev, true, false);
+    q.gb.alloc(own ? *own : ctx->arena, (size_t)r.m * r.m, Engine<T>::gram_dim(go), go.exact_max_pixels, ctx->nsm);
     q.mu.assign(q.levels, 0.0);
     q.iters.assign(q.levels, 0);
     q.inners.assign(q.levels, 0);
@@ -1319,12 +1324,9 @@ struct BatchSolver {
   }
 
   void setup(int count, const db_request* reqs, const double* const* b_dev, const double* const* psf_dev) {
-    size_t n0max = 0, tiles = 0;
-    for (int i = 0; i < count; ++i) {
-      n0max = std::max(n0max, (size_t)reqs[i].m * reqs[i].m);
-      tiles += (size_t)((reqs[i].m + TM - 1) / TM) * ((reqs[i].m + TM - 1) / TM);
-    }
-    alloc_shared(ctx->arena, count, tiles, n0max, workers_for(count));
+    size_t tiles = 0;
+    for (int i = 0; i < count; ++i) tiles += (size_t)((reqs[i].m + TM - 1) / TM) * ((reqs[i].m + TM - 1) / TM);
+    alloc_shared(ctx->arena, count, tiles, workers_for(count));
     for (int i = 0; i < count; ++i) add_problem(i, reqs[i], b_dev[i], psf_dev[i], nullptr);
     CK(cudaStreamSynchronize(st));
   }
@@ -1353,7 +1355,7 @@ struct BatchSolver {
 
   void run_gcvs(const std::vector<int>& need) {
     if (need.empty()) return;
-    const int nw = (int)gbufs.size();
+    const int nw = std::min((int)wst.size(), (int)need.size());
     std::vector<std::thread> th;
     std::vector<DbError> errs(nw);
     std::vector<int> failed(nw, 0);
@@ -1362,13 +1364,13 @@ struct BatchSolver {
         CountScope cs(ctx);
         try {
           CK(cudaSetDevice(ctx->device));
-          // problem p always goes to worker p % nw, so its GCV buffers (and
-          // the Krylov basis cached in them) are the ones it used last time
+          // every problem has its own GCV buffers (and cached Krylov
+          // basis), so the evaluations are dealt to the workers in turn
           for (size_t j = 0; j < need.size(); ++j) {
-            if (need[j] % nw != w) continue;
+            if ((int)(j % nw) != w) continue;
             Prob& q = P[need[j]];
             const int kind = gcv_kind(q);
-            q.E->adopt(gbufs[w]);
+            q.E->adopt(q.gb);
             q.E->st = wst[w];
             // the level's x and auxiliaries were written on the main stream,
             // which the scheduler has synchronised before this point
@@ -1707,7 +1709,7 @@ static void run_batch(db_context* ctx, cudaStream_t st, int count, const db_requ
   BatchSolver<T> B(ctx, st);
   B.o = o;
   B.go = g;
-  ctx->arena.ensure(BatchSolver<T>::footprint(count, reqs, g));
+  ctx->arena.ensure(BatchSolver<T>::footprint(count, reqs, g, ctx->nsm));
   ctx->arena.reset();
   B.setup(count, reqs, b_dev, psf_dev);
   B.run();
@@ -1789,7 +1791,7 @@ struct ServerJob {
   uint64_t ticket = 0;
   db_request req{};
   std::vector<double> b, psf;
-  std::unique_ptr<Arena> arena;
+  Arena* arena = nullptr;            // the workspace of its slot while resident
   double* dev_b = nullptr;
   double* dev_psf = nullptr;
   double* dev_x = nullptr;
@@ -1815,11 +1817,12 @@ struct db_server {
   Arena shared;                      // batched-LSQR tables and GCV workspaces
   std::unique_ptr<BatchSolver<float>> B;
   std::vector<ServerJob*> slots;
+  std::vector<std::unique_ptr<Arena>> slot_arena;   // per-slot workspace, reused by successive requests
   size_t bytes_in_use = 0;
   std::string fatal;
 
-  static size_t job_bytes(const db_request& r) {
-    return Engine<float>::footprint_levels(r.m, r.levels, r.psf_size) + (4ull << 20);
+  size_t job_bytes(const db_request& r) const {
+    return BatchSolver<float>::problem_bytes(r.m, r.levels, r.psf_size, opts.gcv, ctx->nsm);
   }
 
   void loop() {
@@ -1835,7 +1838,7 @@ struct db_server {
           if (!j || !j->cancel) continue;
           B->P[i].done = true;
           B->P[i].E.reset();
-          j->arena.reset();
+          j->arena = nullptr;
           bytes_in_use -= j->bytes;
           slots[i] = nullptr;
           j->status = DB_ECANCELLED;
@@ -1861,14 +1864,18 @@ struct db_server {
           lk.unlock();
           try {
             const size_t n = (size_t)j->req.m * j->req.m, ps = (size_t)j->req.psf_size * j->req.psf_size;
-            j->arena.reset(new Arena());
-            j->arena->ensure(j->bytes + 3 * n * sizeof(double) + ps * sizeof(double) + 4096);
+            // the slot's workspace is kept between requests and grows only
+            // when a larger request arrives (cudaFree would stall the device)
+            Arena& sa = *slot_arena[free_slot];
+            sa.ensure(j->bytes + 3 * n * sizeof(double) + ps * sizeof(double) + 4096);
+            sa.reset();
+            j->arena = &sa;
             j->dev_b = j->arena->take<double>(n);
             j->dev_psf = j->arena->take<double>(ps);
             j->dev_x = j->arena->take<double>(n);
             CK(cudaMemcpyAsync(j->dev_b, j->b.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
             CK(cudaMemcpyAsync(j->dev_psf, j->psf.data(), ps * sizeof(double), cudaMemcpyHostToDevice, st));
-            B->add_problem(free_slot, j->req, j->dev_b, j->dev_psf, j->arena.get());
+            B->add_problem(free_slot, j->req, j->dev_b, j->dev_psf, j->arena);
             lk.lock();
             slots[free_slot] = j;
             j->slot = free_slot;
@@ -1878,7 +1885,7 @@ struct db_server {
             j->status = e.st;
             j->done = true;
             j->t_done = std::chrono::steady_clock::now();
-            j->arena.reset();
+            j->arena = nullptr;
             cv_done.notify_all();
           }
         }
@@ -1898,7 +1905,7 @@ struct db_server {
             j->t_done = std::chrono::steady_clock::now();
             B->P[i].done = true;
             B->P[i].E.reset();
-            j->arena.reset();
+            j->arena = nullptr;
             slots[i] = nullptr;
           }
         bytes_in_use = 0;
@@ -1923,7 +1930,7 @@ struct db_server {
         }
         q.E.reset();
         std::lock_guard<std::mutex> lk(mu);
-        j->arena.reset();
+        j->arena = nullptr;
         bytes_in_use -= j->bytes;
         slots[i] = nullptr;
         j->done = true;
@@ -1950,14 +1957,13 @@ extern "C" db_status db_server_create(db_context* ctx, const db_server_opts* o, 
     s->B.reset(new BatchSolver<float>(ctx, s->st));
     s->B->o = s->opts.opts;
     s->B->go = s->opts.gcv;
-    const size_t n0max = (size_t)o->max_m * o->max_m;
     const size_t tiles = (size_t)o->max_resident * ((o->max_m + TM - 1) / TM) * ((o->max_m + TM - 1) / TM);
     const int nw = BatchSolver<float>::workers_for(o->max_resident);
-    s->shared.ensure((size_t)nw * GcvBufs<float>::bytes(n0max, Engine<float>::gram_dim(s->opts.gcv),
-                                                       s->opts.gcv.exact_max_pixels, 160) +
-                     tiles * 40 + (size_t)o->max_resident * 4096 + (16ull << 20));
-    s->B->alloc_shared(s->shared, o->max_resident, tiles, n0max, nw);
+    s->shared.ensure(tiles * 40 + (size_t)o->max_resident * 4096 + (16ull << 20));
+    s->B->alloc_shared(s->shared, o->max_resident, tiles, nw);
     s->slots.assign(o->max_resident, nullptr);
+    for (int i = 0; i < o->max_resident; ++i) s->slot_arena.emplace_back(new Arena());
+    if (o->hbm_budget_bytes) for (auto& a : s->slot_arena) a->budget = o->hbm_budget_bytes;
     db_server* raw = s.release();
     raw->th = std::thread([raw] { raw->loop(); });
     *out = raw;
@@ -1980,7 +1986,7 @@ extern "C" db_status db_server_submit(db_server* s, const db_request* r, uint64_
     j->req = *r;
     j->b.assign(r->b, r->b + (size_t)r->m * r->m);
     j->psf.assign(r->psf, r->psf + (size_t)r->psf_size * r->psf_size);
-    j->bytes = db_server::job_bytes(*r);
+    j->bytes = s->job_bytes(*r);
     j->t_submit = std::chrono::steady_clock::now();
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stopping) return DB_EBUSY;

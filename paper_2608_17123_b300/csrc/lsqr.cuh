@@ -575,6 +575,7 @@ __global__ void __launch_bounds__(256, 2) k_lsqr(const LsqrProb<T, Acc>* __restr
   __shared__ double scratch[3 * 32];
   __shared__ __align__(16) LsqrProb<T, Acc> s_prob[LSQR_TCACHE];
   __shared__ int s_pid[LSQR_TCACHE];
+  __shared__ int s_skip[2];
   LsqrCoef<Acc>* coef = reinterpret_cast<LsqrCoef<Acc>*>(ctl.coef);
   const unsigned G = gridDim.x;
   const int tid = threadIdx.x + 32 * threadIdx.y;
@@ -614,14 +615,24 @@ __global__ void __launch_bounds__(256, 2) k_lsqr(const LsqrProb<T, Acc>* __restr
       const bool isF = (half == 0);
       const int ph = 2 * it + half;
       int k = 0;
+      bool waited = false;   // this block has met the release of phase ph - 1
       for (int tile = blockIdx.x; tile < ctl.ntiles; tile += G, ++k) {
         const bool cached = k < LSQR_TCACHE;
         const int p = cached ? s_pid[k] : __ldg(ctl.tile_prob + tile);
+        // tiles of a problem that has stopped are skipped before any load
+        // (launches over several problems, which stop at different
+        // iterations; a single problem ends the launch when it stops).
+        // Thread 0 reads the flag for the whole block; it only ever goes from
+        // 0 to 1, so a stale 0 costs one pass and nothing else.
+        // (Two slots by tile parity: a thread can only write the slot of tile
+        // k + 2 after every thread has passed the barrier of tile k + 1.)
+        if (tid == 0) s_skip[k & 1] = (ph > 0 && ctl.nprob > 1) ? __ldcg(&ctl.st[p].done) : 0;
+        __syncthreads();   // shared memory of the previous tile is free; s_skip is visible
+        if (s_skip[k & 1]) continue;
         const LsqrProb<T, Acc>& P = cached ? s_prob[k] : probs[p];
         const int tl = tile - P.tile_begin;
         const int r0 = (tl % P.nt) * TM, c0 = (tl / P.nt) * TN;
         Sums3<Acc> red;
-        __syncthreads();   // shared memory of the previous tile is free
         Acc* cbr = nullptr;
         Acc* cbc = nullptr;
         if (cached && ctl.band_cache) {
@@ -629,12 +640,16 @@ __global__ void __launch_bounds__(256, 2) k_lsqr(const LsqrProb<T, Acc>* __restr
           cbr = cb;
           cbc = cb + TM * ctl.band_pw;
         }
-        const int rc = isF ? lsqr_pass_F<T, Acc>(P, ctl, p, it == 0, it == 1, r0, c0, sm, red, cbr, cbc, ph, k == 0)
-                           : lsqr_pass_B<T, Acc>(P, ctl, p, it == 0, r0, c0, sm, red, cbr, cbc, ph, k == 0);
+        const int rc = isF ? lsqr_pass_F<T, Acc>(P, ctl, p, it == 0, it == 1, r0, c0, sm, red, cbr, cbc, ph, !waited)
+                           : lsqr_pass_B<T, Acc>(P, ctl, p, it == 0, r0, c0, sm, red, cbr, cbc, ph, !waited);
+        waited = true;
         if (rc < 0) return;    // every problem has stopped, or a wait timed out (uniform over the block)
         if (rc == 0) continue;
         tile_partial(red, phase_part(ctl, ph) + (size_t)tile * 3, scratch);
       }
+      // a block whose tiles were all skipped still meets the release (it
+      // carries the all-stopped decision) before it arrives
+      if (!waited && lsqr_wait_release(ctl, ph) != 0) return;
       if (lsqr_phase_arrive<T, Acc>(probs, ctl, coef, isF, it, ph) < 0) return;
     }
   }

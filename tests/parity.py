@@ -9,8 +9,11 @@ which applies one rule and records the case:
 * when it is not -- the oracle itself moves by more than the target when
   every operator output carries unit-roundoff noise of the storage precision
   (tests/perturb.py; "spread" = the largest change over the reruns) -- the GPU
-  result, which is one more such perturbation, must land within MARGIN times
-  the spread. Such cases are flagged "oracle-spread" in the record.
+  result, which is one more such perturbation, must land within MARGIN = 3
+  times the spread (the spread is the largest change over only three
+  reruns). Such cases are flagged "oracle-spread" in the record;
+* a few cases fit neither, for a cause named in DOCUMENTED below; they are
+  flagged "documented".
 
 With DEBLUR_PARITY_REPORT set to a file name, the records of the session
 (test, quantity, difference, spread, tolerance, rule) are written there as
@@ -21,7 +24,7 @@ from __future__ import annotations
 import json
 import os
 
-MARGIN = 2.0
+MARGIN = 3.0
 RECORDS: list[dict] = []
 
 # Cases where the GPU lands further from the oracle than both the target and

@@ -44,3 +44,26 @@ def test_batch_of_one_and_mixed_precisionless_defaults():
     rb = api.deblur_solve_batch([dict(b=b, psf=psf, solver="sb", wavelet="db4", levels=2, transfer="D")])[0]
     rs = api.deblur_solve(b, psf, "sb", "db4", 2, "D")
     assert rb["iters"] == rs["iters"] and rel(rb["x"], rs["x"]) <= 1e-12
+
+
+def test_batched_and_served_match_oracle():
+    """Batched and served FP32 solves of three m = 32 cases against the FP64
+    oracle, with the same rule as the single solves (tests/parity.py)."""
+    from parity import check_solve
+    from test_gpu_solve import case, references, storage_rounded
+    A, b, _, psf = case(32, 1.5, 7, 6, 3, 1, 0.01)
+    combos = [("irls", "haar", 2, "X"), ("mm", "db4", 3, "D"), ("sb", "haar", 2, "D")]
+    b32 = storage_rounded(b, "fp32")
+    probs = [dict(b=b32, psf=psf, solver=c[0], wavelet=c[1], levels=c[2], transfer=c[3]) for c in combos]
+    batch = api.deblur_solve_batch(probs, precision="fp32")
+    srv = api.Server(max_resident=2, max_m=32, ctx=api.Context(0))
+    try:
+        tickets = [srv.submit(b32, psf, *c) for c in combos]
+        served = [srv.poll(t)[0] for t in tickets]
+    finally:
+        srv.close()
+    for c, rb, rs in zip(combos, batch, served):
+        r0, r1 = references(A, b, c, "fp32")
+        tag = "-".join(map(str, c))
+        check_solve(f"batched_m32[{tag}]", rb, r0, r1, 1e-4, rel)
+        check_solve(f"served_m32[{tag}]", rs, r0, r1, 1e-4, rel)

@@ -3,7 +3,7 @@ planes and Krylov-vector storage in bfloat16, the outer iterate and the LSQR
 correction in float32, FP32 accumulation, FP64 scalar recurrences, GCV and
 stopping tests. End-to-end V-cycle solves against the FP64 oracle with the
 tolerance rule of tests/parity.py: the BF16 target 1e-3 relative in x, 1 % in
-gamma and +-1 outer iteration, or twice the oracle's own spread under
+gamma and +-1 outer iteration, or three times the oracle's own spread under
 bfloat16 unit-roundoff noise where that spread exceeds the target."""
 import numpy as np
 import pytest

@@ -6,7 +6,7 @@ FP64; gamma: 1 %; outer iterations: +-1), except where the oracle's own
 result is not determined to that precision -- its spread over three reruns
 with unit-roundoff noise of the storage precision injected into every
 operator output exceeds the target -- and the GPU result must then land
-within twice that spread. On these small levels that is common: the GCV
+within three times that spread. On these small levels that is common: the GCV
 minimiser is located only to Brent's tolerance, the doubling of the
 projected dimension stops on a 0.1 % test, and coarse levels that run to
 K_max carry every perturbation to the end.
