@@ -1,28 +1,31 @@
 #!/usr/bin/env python
 """Throughput of the wavelet multilevel l1-deblurring V-cycle on one B300.
 
-Workload (one "step" = one complete V-cycle solve, Alg. 4, of one image):
-the m = 512 workload -- a 512 x 512 synthetic piecewise-constant phantom
-(40 rectangles, 20 disks, intensities U[0,1], seed 0), Gaussian PSF
-sigma = 3 on 15 x 15, b = A x_true + noise at 1 % (even blocks of 12 steps)
-or 5 % (odd blocks), rounded to float32; 3-level cycles; step s runs
-combination s mod 12 of {IRLS, MM, SB} x {Haar, Db4} x {X, D}. FP32 storage;
-the LSQR and Krylov sums are compensated float pairs (double-float) turned
-into double, the scalar recurrences, GCV selection and stopping tests are
-FP64.
+Workload: the m = 512 workload -- a 512 x 512 synthetic piecewise-constant
+phantom (40 rectangles, 20 disks, intensities U[0,1], seed 0), Gaussian PSF
+sigma = 3 on 15 x 15, b = A x_true + noise at 1 % or 5 %, rounded to float32,
+deblurred by 3-level V-cycles (Alg. 4) under all 12 combinations of
+{IRLS, MM, SB} x {Haar, Db4} x {X, D}. FP32 storage; LSQR norms and Krylov
+dot products as double-float sums of exact products; scalar recurrences, GCV
+selection and stopping tests in FP64.
 
+One step = one batch: the 12 combinations of one noise level (1 % on even
+steps, 5 % on odd steps) in one deblur_solve_batch call on device buffers.
 Metric: deblurred Mpixel/s (whole job, all ranks). Inputs are resident in
 HBM when the timed region starts; L2 is flushed (256 MB write) before every
-step, outside the CUDA-event pair that times it. `e2e` repeats the same
-steps through the host-buffer C-ABI call (pinned host input, host->device
-and device->host copies inside the timed region). `oracle_parity` compares
-every timed step with the FP64 oracle's stored result of the same case
-(tests/golden/m512_oracle). `large` times a few solves of the large-image
-workload: m = 2048, Gaussian sigma = 6 on 31 x 31 and the 21-pixel motion
-blur at 30 degrees, BF16 storage, 5-level Db4 cycles.
+step, outside the CUDA-event pair that times it.
 
-`--impl reference` times the FP64 CPU oracle on a bounded sample of the
-same workload (see oracle_sample()).
+Beside it on the same line: `plain` (the same 12 images, one deblur_solve
+each), `e2e` (the same batches through the host-buffer call: copies in and
+out inside the timed region), `oracle_parity` (every case against the FP64
+oracle's stored result, tests/golden/m512_oracle), `serving` (the server
+under all-at-once and Poisson arrivals, p50/p99), `large` (m = 2048, BF16,
+5-level Db4 solves of the Gaussian 31 x 31 and 21-pixel motion blurs), and
+`cpu_baseline`.
+
+Other modes: --workload batch | serve | study (see their functions), and
+--impl reference: the FP64 CPU oracle on a bounded sample of the workload
+(see run_reference()).
 """
 from __future__ import annotations
 
@@ -79,6 +82,7 @@ def workload_desc():
             "levels": LEVELS, "combos": "irls/mm/sb x haar/db4 x X/D", "noise": "1%,5%", "seed": SEED,
             "phantom": "40 rect + 20 disk", "precision": "fp32 storage, double-float (compensated fp32) sums, "
             "fp64 scalar recurrences / GCV / stopping tests",
+            "step": "one deblur_solve_batch call: the 12 combinations at one noise level",
             "l2": "flushed (256 MB write) before every step"}
 
 
@@ -225,6 +229,11 @@ def parity_summary(results, golden):
 
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world):
+    """Timed steps: each step deblurs one batch -- the 512 x 512 phantom at one
+    noise level (1 % on even steps, 5 % on odd ones) under all 12
+    solver / wavelet / transfer combinations -- in one deblur_solve_batch
+    call on device buffers. The same 12 images one at a time (deblur_solve)
+    give the plain figures beside it."""
     import torch
     from paper_2608_17123_b300 import api
     from paper_2608_17123_b300 import inputs as I
@@ -239,22 +248,21 @@ def run_ours(args, rank, world):
     steps = shard_steps(rank, args.warmup, args.steps)
     x_true = I.phantom(M, 40, 20, SEED)
     bs = {nz: make_b(api, torch, M, x_true, psf, nz, 10_000 + SEED) for nz in NOISES}
-    # inputs resident in HBM before timing
-    dev_inputs, host_inputs = [], []
-    for s in steps:
-        b = bs[step_spec(s)[3]]
-        dev_inputs.append(torch.from_numpy(I.to_colmajor(b).ravel()).cuda())
-        host_inputs.append(I.to_colmajor(b).ravel())
-    x_out = [torch.empty(M * M, dtype=torch.float64, device="cuda") for _ in range(args.steps)]
-    x_warm = torch.empty(M * M, dtype=torch.float64, device="cuda")
+    b_dev = {nz: torch.from_numpy(I.to_colmajor(b).ravel()).cuda() for nz, b in bs.items()}
+    nb = len(COMBOS)
+    xs = [torch.empty(M * M, dtype=torch.float64, device="cuda") for _ in range(nb)]
 
-    def solve_dev(i, xd):
-        solver, wavelet, transfer, _ = step_spec(steps[i])
-        return api.deblur_solve_device(dev_inputs[i], psf_dev, M, PSF_SIZE, xd, solver, wavelet, LEVELS, transfer,
-                                       precision="fp32", ctx=ctx, stream=stream.cuda_stream)
+    def noise_of(s):
+        return NOISES[s % 2]
+
+    def batch_dev(s):
+        nz = noise_of(s)
+        probs = [dict(b=b_dev[nz], psf=psf_dev, x=xs[j], m=M, psf_size=PSF_SIZE, solver=c[0], wavelet=c[1],
+                      levels=LEVELS, transfer=c[2]) for j, c in enumerate(COMBOS)]
+        return api.deblur_solve_batch_device(probs, precision="fp32", ctx=ctx, stream=stream.cuda_stream)
 
     for i in range(args.warmup):
-        solve_dev(i, x_warm)
+        batch_dev(steps[i])
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
@@ -263,19 +271,23 @@ def run_ours(args, rank, world):
     ctx.reset_stats()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    times, results = [], []
-    for k, i in enumerate(range(args.warmup, total)):
+    times, par_in, seen = [], [], set()
+    for i in range(args.warmup, total):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         torch.cuda.nvtx.range_push("timed")     # lets a profiler select exactly the timed steps
-        r = solve_dev(i, x_out[k])
+        res = batch_dev(steps[i])
         torch.cuda.nvtx.range_pop()
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
-        results.append((steps[i], r))
+        nz = noise_of(steps[i])
+        if nz not in seen:                       # each case once, for the oracle comparison
+            seen.add(nz)
+            for j, c in enumerate(COMBOS):
+                par_in.append((case_name(c[0], c[1], c[2], nz), xs[j].cpu().numpy(), res[j]["iters"], res[j]["mu"]))
     torch.cuda.synchronize()
     clk = clocks.stop()
     stats = ctx.stats()
@@ -283,58 +295,57 @@ def run_ours(args, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    pixels = M * M * args.steps * world
-    value = pixels / (t_total_ms / 1e3) / 1e6
-
-    # the reconstructions of the timed steps against the FP64 oracle
-    par_in = []
-    for k, (s, r) in enumerate(results):
-        solver, wavelet, transfer, noise = step_spec(s)
-        par_in.append((case_name(solver, wavelet, transfer, noise), x_out[k].cpu().numpy(), r["iters"], r["mu"]))
+    images = nb * args.steps * world
+    value = M * M * images / (t_total_ms / 1e3) / 1e6
     parity = parity_summary(par_in, load_golden())
 
-    # e2e: the same steps through the host-buffer call (pinned input; copies
+    # plain: the same 12 images of the first timed step, one deblur_solve each
+    s0 = steps[args.warmup]
+    plain_ms = 0.0
+    for j, c in enumerate(COMBOS):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        api.deblur_solve_device(b_dev[noise_of(s0)], psf_dev, M, PSF_SIZE, xs[j], c[0], c[1], LEVELS, c[2],
+                                precision="fp32", ctx=ctx, stream=stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        plain_ms += e0.elapsed_time(e1)
+
+    # e2e: the same batches through the host-buffer call (copies in and out
     # inside the timed region); --e2e-steps 0 skips it (profiling runs only)
     e2e_steps = args.steps if args.e2e_steps < 0 else min(args.steps, args.e2e_steps)
-    pinned_b = [torch.from_numpy(host_inputs[args.warmup + i]).pin_memory() for i in range(e2e_steps)]
-    psf_host = torch.from_numpy(I.to_colmajor(psf).ravel()).pin_memory()
-    x_host = torch.empty(M * M, dtype=torch.float64).pin_memory()
-    import ctypes as C
-    from paper_2608_17123_b300 import _lib as L
     e2e_ms = 0.0
     for i in range(e2e_steps):
-        solver, wavelet, transfer, _ = step_spec(steps[args.warmup + i])
-        o, g = api.make_opts("fp32")
-        mu = np.zeros(LEVELS)
-        it = np.zeros(LEVELS, dtype=np.int32)
+        nz = noise_of(steps[args.warmup + i])
+        probs = [dict(b=bs[nz], psf=psf, solver=c[0], wavelet=c[1], levels=LEVELS, transfer=c[2]) for c in COMBOS]
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st = L.lib().deblur_solve(ctx.handle, C.c_void_p(pinned_b[i].data_ptr()), M, C.c_void_p(psf_host.data_ptr()),
-                                  PSF_SIZE, L.SOLVERS[solver], L.WAVELETS[wavelet], LEVELS, L.TRANSFERS[transfer],
-                                  C.byref(g), C.byref(o), C.c_void_p(x_host.data_ptr()), mu.ctypes.data,
-                                  it.ctypes.data, None, 0, C.c_void_p(stream.cuda_stream))
-        L.check(st, ctx.handle)
+        api.deblur_solve_batch(probs, precision="fp32", ctx=ctx, stream=stream.cuda_stream)
         e2e_ms += (time.perf_counter() - t0) * 1e3
-    e2e_value = M * M * e2e_steps * world / (e2e_ms / 1e3) / 1e6 if e2e_steps else None
+    e2e_value = M * M * nb * e2e_steps * world / (e2e_ms / 1e3) / 1e6 if e2e_steps else None
 
-    # roofline of k_lsqr on this workload (finest-level launches)
     peak, peak_kind = load_peaks()
-    roofline = lsqr_roofline(stats, 4, 4, peak, peak_kind, t_total_ms, "m512",
-                             note="the level's LSQR vectors (~20 MB) stay in the 126 MB L2: latency- and "
-                                  "barrier-bound, not HBM-bound, at this size")
-
+    roofline = lsqr_roofline_all(stats, 4, 4, peak, peak_kind, t_total_ms, "m512",
+                                 note="batched launches over the 12 problems of a step, every level; the vectors "
+                                      "of 12 m = 512 cycles (~250 MB) exceed the 126 MB L2 only in part")
     line = {
         "metric": "deblurred Mpixel/s", "value": round(value, 4), "unit": "Mpixel/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_total_ms / args.steps, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "images_per_step": nb, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic phantoms (inputs module), b = A x_true by the library's blur + seeded noise, "
                 "rounded to float32",
         "config": workload_desc(),
-        "images_per_s": round(args.steps * world / (t_total_ms / 1e3), 4),
+        "images_per_s": round(images / (t_total_ms / 1e3), 4),
+        "plain": {"images_per_s": round(nb / (plain_ms / 1e3), 4),
+                  "mpixel_per_s": round(M * M * nb / (plain_ms / 1e3) / 1e6, 4),
+                  "ms_per_image": round(plain_ms / nb, 1), "call": "deblur_solve, one image at a time"},
         "e2e": None if e2e_value is None else
                {"value": round(e2e_value, 4), "unit": "Mpixel/s", "steps": e2e_steps,
-                "h2d_bytes_per_step": M * M * 8 + PSF_SIZE * PSF_SIZE * 8, "d2h_bytes_per_step": M * M * 8 + LEVELS * 12},
+                "h2d_bytes_per_step": nb * (M * M * 8 + PSF_SIZE * PSF_SIZE * 8),
+                "d2h_bytes_per_step": nb * (M * M * 8 + LEVELS * 16)},
         "gpu_launches": int(stats["kernel_launches"]),
         "roofline": roofline,
         "oracle_parity": parity,
@@ -342,14 +353,67 @@ def run_ours(args, rank, world):
         "counts": {"lsqr_launches": int(stats["lsqr_launches"]), "gcv_calls": int(stats["gcv_calls"]),
                    "outer_iterations": int(stats["outer_iterations"])},
         "step_split": {"lsqr_ms_per_step": round(stats["lsqr_ms"] / args.steps, 2),
-                       "gcv_ms_per_step": round(stats.get("gcv_ms", 0.0) / args.steps, 2)},
+                       "gcv_ms_per_step": round(stats.get("gcv_ms", 0.0) / args.steps, 2),
+                       "note": "GCV time is host wall time summed over the worker threads"},
     }
     if world == 1 and args.large_steps > 0:
         line["large"] = run_large(api, torch, ctx, args.large_steps, flush, peak, peak_kind)
     if world == 1 and args.forms:
-        line.update(run_forms(api, ctx, torch, [host_inputs[args.warmup + i] for i in range(args.steps)],
-                              [steps[args.warmup + i] for i in range(args.steps)], psf))
-    return line, results
+        line["serving"] = run_serving_m512(api, ctx, bs, psf)
+    return line, [n for n, _, _, _ in par_in]
+
+
+def lsqr_roofline_all(stats, elem, x_elem, peak, peak_kind, t_total_ms, key, note):
+    """achieved = algorithmic bytes of every k_lsqr launch of the timed
+    region / their CUDA-event time (event pair around each launch on the
+    solve's stream)."""
+    bytes_alg = (stats["lsqr_pixel_iters_irls"] * lsqr_bytes_per_pixel_iter(elem, x_elem, True)
+                 + stats["lsqr_pixel_iters_other"] * lsqr_bytes_per_pixel_iter(elem, x_elem, False))
+    launches = max(1, stats["lsqr_launches"])
+    ms = stats["lsqr_ms"]
+    achieved = (bytes_alg / launches) / ((ms / launches) / 1e3) / 1e9 if ms > 0 else 0.0
+    traffic, scope = LSQR_DRAM[key]
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic, "traffic_scope": scope,
+            "algorithmic_bytes_per_launch": round(bytes_alg / launches),
+            "kernel": "k_lsqr (persistent cooperative LSQR), every launch of the timed region",
+            "launches": int(stats["lsqr_launches"]), "peak_kind": peak_kind,
+            "lsqr_share_of_step": round(ms / t_total_ms, 4) if t_total_ms else None, "note": note}
+
+
+def run_serving_m512(api, ctx, bs, psf):
+    """Poisson arrivals of the 24 cases (12 combinations x 2 noise levels, each
+    twice) at 80 % of the server's saturated rate, measured first with every
+    request queued at once; p50 / p99 latency from submit to completion."""
+    reqs = [(bs[nz], c) for nz in NOISES for c in COMBOS]
+    srv = api.Server(max_resident=len(reqs), max_m=M, ctx=api.Context(0))
+    t0 = time.perf_counter()
+    tks = [srv.submit(b, psf, c[0], c[1], LEVELS, c[2]) for b, c in reqs]
+    lat_all = [srv.poll(tk)[1] for tk in tks]
+    t_sat = time.perf_counter() - t0
+    srv.close()
+    sat = len(reqs) / t_sat
+    rng = np.random.default_rng(2026)
+    order = [i % len(reqs) for i in range(2 * len(reqs))]
+    gaps = rng.exponential(1.0 / (0.8 * sat), size=len(order))
+    srv = api.Server(max_resident=len(reqs), max_m=M, ctx=api.Context(0))
+    t0 = time.perf_counter()
+    tks, t_next = [], 0.0
+    for k, i in enumerate(order):
+        t_next += gaps[k]
+        while time.perf_counter() - t0 < t_next:
+            time.sleep(0.0005)
+        b, c = reqs[i]
+        tks.append(srv.submit(b, psf, c[0], c[1], LEVELS, c[2]))
+    lat = [srv.poll(tk)[1] for tk in tks]
+    t_p = time.perf_counter() - t0
+    srv.close()
+    return {"saturated_images_per_s": round(sat, 4), "requests": len(reqs),
+            "all_queued_p50_ms": round(float(np.percentile(lat_all, 50)), 1),
+            "poisson": {"rate_per_s": round(0.8 * sat, 3), "requests": len(order),
+                        "images_per_s": round(len(order) / t_p, 4),
+                        "p50_ms": round(float(np.percentile(lat, 50)), 1),
+                        "p99_ms": round(float(np.percentile(lat, 99)), 1)}}
 
 
 def lsqr_roofline(stats, elem, x_elem, peak, peak_kind, t_total_ms, key, note):
@@ -422,72 +486,6 @@ def run_large(api, torch, ctx, nsteps, flush, peak, peak_kind):
                                            "L2 size"),
             "step_split": {"lsqr_ms_per_step": round(stats["lsqr_ms"] / nsteps, 1),
                            "gcv_ms_per_step": round(stats.get("gcv_ms", 0.0) / nsteps, 1)}}
-
-
-def run_forms(api, ctx, torch, bs, step_ids, psf):
-    """Images/s of the plain one-at-a-time host call, the batched call
-    (deblur_solve_batch) and the serving loop (db_server_*, all requests
-    queued at once) on the same images, with the largest relative difference
-    of the batched and served reconstructions from the plain ones; then a
-    Poisson request stream at 80 % of the batched throughput (each image
-    twice) with its p50/p99 latency."""
-    from paper_2608_17123_b300 import inputs as I
-    imgs = [I.from_colmajor(b, M) for b in bs]
-    specs = [step_spec(s) for s in step_ids]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    plain = [api.deblur_solve(b, psf, sp[0], sp[1], LEVELS, sp[2], precision="fp32", ctx=ctx)
-             for b, sp in zip(imgs, specs)]
-    t_plain = time.perf_counter() - t0
-    probs = [dict(b=b, psf=psf, solver=sp[0], wavelet=sp[1], levels=LEVELS, transfer=sp[2])
-             for b, sp in zip(imgs, specs)]
-    t0 = time.perf_counter()
-    batched = api.deblur_solve_batch(probs, precision="fp32", ctx=ctx)
-    t_batch = time.perf_counter() - t0
-    srv = api.Server(max_resident=len(imgs), max_m=M)
-    t0 = time.perf_counter()
-    tickets = [srv.submit(b, psf, sp[0], sp[1], LEVELS, sp[2]) for b, sp in zip(imgs, specs)]
-    served, lat = [], []
-    for tk in tickets:
-        r, l = srv.poll(tk)
-        served.append(r)
-        lat.append(l)
-    t_srv = time.perf_counter() - t0
-    srv.close()
-
-    def rel(a, b):
-        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-
-    rng = np.random.default_rng(2026)
-    rate = 0.8 * len(imgs) / t_batch
-    order = [i % len(imgs) for i in range(2 * len(imgs))]
-    gaps = rng.exponential(1.0 / rate, size=len(order))
-    srv = api.Server(max_resident=len(imgs), max_m=M)
-    t0 = time.perf_counter()
-    tks, t_next = [], 0.0
-    for k, i in enumerate(order):
-        t_next += gaps[k]
-        while time.perf_counter() - t0 < t_next:
-            time.sleep(0.0005)
-        sp = specs[i]
-        tks.append(srv.submit(imgs[i], psf, sp[0], sp[1], LEVELS, sp[2]))
-    lat_p = [srv.poll(tk)[1] for tk in tks]
-    t_poisson = time.perf_counter() - t0
-    srv.close()
-    n = len(imgs)
-    lat_sorted = sorted(lat)
-    poisson = {"rate_per_s": round(rate, 3), "requests": len(order), "images_per_s": round(len(order) / t_poisson, 4),
-               "p50_ms": round(float(np.percentile(lat_p, 50)), 2), "p99_ms": round(float(np.percentile(lat_p, 99)), 2)}
-    return {
-        "plain_images_per_s": round(n / t_plain, 4),
-        "batched": {"images_per_s": round(n / t_batch, 4), "images": n, "call": "deblur_solve_batch",
-                    "max_rel_diff_vs_plain": max(rel(b["x"], p["x"]) for b, p in zip(batched, plain))},
-        "serving": {"images_per_s": round(n / t_srv, 4), "requests": n, "arrival": "all queued at t=0",
-                    "p50_ms": round(float(np.percentile(lat_sorted, 50)), 2),
-                    "p99_ms": round(float(np.percentile(lat_sorted, 99)), 2),
-                    "max_rel_diff_vs_plain": max(rel(q["x"], p["x"]) for q, p in zip(served, plain)),
-                    "poisson": poisson},
-    }
 
 
 # ------------------------------------------------------------------ oracle sample
@@ -629,7 +627,7 @@ def run_reference(args, rank, world):
     golden = load_golden()
     if golden is None:
         return {"impl": "reference", "unavailable": "stored oracle counts (tests/golden/m512_oracle) missing"}
-    names = [case_name(*step_spec(s)) for s in range(args.warmup, args.warmup + args.steps)]
+    names = [case_name(c[0], c[1], c[2], nz) for nz in NOISES for c in COMBOS]
     names = [n for n in names if n in golden["cases"]]
     for s in range(args.warmup):
         sample_unit_costs((s % LEVELS,), lsqr_iters=(2, 4, 8))
@@ -784,6 +782,41 @@ def run_serve_workload(args):
             "max_rel_diff_served_vs_plain": worst, "precision": "fp32"}
 
 
+# ------------------------------------------------------------------ single LSQR launches
+def run_lsqr_probe(args):
+    """Four LSQR solves of one level-0 MM subproblem (gamma = 1e-3, 100
+    iterations, stopping tolerances off) on an m x m phantom with the given
+    PSF, FP32, autotuning off: one k_lsqr launch each. The profiler
+    recipes of profiles/ capture the fourth launch (-k regex:k_lsqr -s 3 -c 1)."""
+    import torch
+    from paper_2608_17123_b300 import api
+    from paper_2608_17123_b300 import inputs as I
+    m = args.lsqr_m
+    psf = I.gaussian_psf(*{"gauss31": (6.0, 31), "gauss15": (3.0, 15)}[args.lsqr_psf])
+    ctx = api.Context(0)
+    ctx.set_autotune(False)
+    xt = torch.from_numpy(I.to_colmajor(I.phantom(m, 40, 20, 6)).ravel()).to("cuda", torch.float32)
+    b = torch.empty_like(xt)
+    api.apply_blur(psf, m, xt, b, ctx=ctx)
+    x0 = 0.9 * xt
+    c = torch.zeros(2 * m * m, device="cuda", dtype=torch.float32)
+    xo = torch.empty_like(xt)
+    for _ in range(3):
+        api.lsqr_solve(psf, m, "mm", 1e-3, b, x0, c, None, xo, ctx=ctx, lsqr_maxit=100, lsqr_atol=0.0, lsqr_btol=0.0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    its = api.lsqr_solve(psf, m, "mm", 1e-3, b, x0, c, None, xo, ctx=ctx, lsqr_maxit=100, lsqr_atol=0.0,
+                         lsqr_btol=0.0)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.close()
+    alg = (its + 1) * m * m * lsqr_bytes_per_pixel_iter(4, 4, False)
+    return {"probe": "lsqr", "m": m, "psf": args.lsqr_psf, "iterations": its, "ms": round(ms, 3),
+            "us_per_iteration": round(1e3 * ms / its, 2), "algorithmic_gb_s": round(alg / ms / 1e6, 1)}
+
+
 # ------------------------------------------------------------------ phantom study
 def ssim(x, y, L=None, win=11, sigma=1.5):
     """Structural similarity index (Wang, Bovik, Sheikh, Simoncelli 2004):
@@ -850,25 +883,28 @@ def run_phantom_study(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=24)
+    ap.add_argument("--steps", type=int, default=6)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=-1, help="-1: every timed step")
     ap.add_argument("--large-steps", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", dest="forms", action="store_false",
-                    help="skip the batched / serving comparison")
-    ap.add_argument("--workload", default="m512", choices=["m512", "batch", "serve", "study"],
+                    help="skip the serving measurement")
+    ap.add_argument("--lsqr-m", type=int, default=2048)
+    ap.add_argument("--lsqr-psf", default="gauss31", choices=["gauss31", "gauss15"])
+    ap.add_argument("--workload", default="m512", choices=["m512", "batch", "serve", "study", "lsqr"],
                     help="m512: the benchmark line; batch: 64 uneven images batched vs one at a time; "
                          "serve: Poisson request stream against the server; study: the phantom study of "
-                         "the paper's experiments")
+                         "the paper's experiments; lsqr: four single-level LSQR launches (profiling)")
     ap.add_argument("--batch-images", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 1.0, 2.0, 4.0])
     args = ap.parse_args()
     if args.workload != "m512":
-        fn = {"batch": run_batch_workload, "serve": run_serve_workload, "study": run_phantom_study}[args.workload]
+        fn = {"batch": run_batch_workload, "serve": run_serve_workload, "study": run_phantom_study,
+              "lsqr": run_lsqr_probe}[args.workload]
         print(json.dumps(fn(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -883,10 +919,9 @@ def main():
         if line is not None:
             print(json.dumps(line), flush=True)
         return
-    line, results = run_ours(args, rank, world)
+    line, names = run_ours(args, rank, world)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            names = [case_name(*step_spec(s)) for s, _ in results]
             line["cpu_baseline"] = oracle_sample(names)
         print(json.dumps(line), flush=True)
     if world > 1:

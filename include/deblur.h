@@ -154,13 +154,15 @@ db_status deblur_solve_batch(db_context* ctx, int count, const db_request* reqs,
 
 /* ---- serving loop (an addition of this library, not in the paper) ---------
  * Continuous batching of deblur solves: a scheduler thread keeps up to
- * `max_resident` solves resident on the device (each with its own device
- * arena holding its V-cycle state) and advances all of them one outer
- * iteration per step, exactly as deblur_solve_batch does; a submitted request
- * is admitted at the next step boundary once a slot is free and its device
- * footprint (db_footprint_bytes without the shared GCV workspace) fits the
- * budget. Results are identical to a separate deblur_solve of the same
- * request (same kernels and per-problem arithmetic).
+ * `max_resident` solves resident on the device and advances all of them one
+ * outer iteration per step, exactly as deblur_solve_batch does; a submitted
+ * request is admitted at the next step boundary once a slot is free and its
+ * device footprint (its V-cycle state and its GCV workspace) fits the
+ * budget. Each slot keeps its device workspace for the server's lifetime and
+ * grows it only when a larger request arrives: once every slot has served a
+ * request of the largest size, admitting and retiring requests allocates and
+ * frees nothing. Results are identical to a separate deblur_solve of the
+ * same request (same kernels and per-problem arithmetic).
  * Requests use host buffers: submit copies b and psf; x, mu, iters (and
  * inner if not NULL) are written into the request's host buffers before the
  * request is reported done; they must stay valid until then. FP32 storage.

@@ -142,6 +142,32 @@ def deblur_solve_batch(problems, precision="fp32", ctx=None, stream=None, **opti
             for (m, x, mu, it, inner) in outs]
 
 
+def deblur_solve_batch_device(problems, precision="fp32", ctx=None, stream=None, **options):
+    """Batched solves on device buffers. ``problems``: list of dicts with keys
+    b, psf, x (torch float64 CUDA tensors, column-major), m, psf_size, solver,
+    wavelet, levels, transfer. Returns per problem dict(mu, iters, inner)."""
+    ctx = ctx or default_context()
+    o, g = make_opts(precision, **options)
+    reqs, outs = (L.DbRequest * len(problems))(), []
+    for i, pr in enumerate(problems):
+        lv = pr.get("levels", 2)
+        mu = np.zeros(lv)
+        it = np.zeros(lv, dtype=np.int32)
+        inner = np.zeros(lv, dtype=np.int32)
+        r = reqs[i]
+        r.b, r.m, r.psf, r.psf_size = pr["b"].data_ptr(), pr["m"], pr["psf"].data_ptr(), pr["psf_size"]
+        r.solver = L.SOLVERS[pr.get("solver", "irls")]
+        r.wavelet = L.WAVELETS[pr.get("wavelet", "haar")]
+        r.levels = lv
+        r.transfer = L.TRANSFERS[pr.get("transfer", "X")]
+        r.x, r.mu_per_level, r.iters_per_level, r.inner_iters_per_level = (
+            pr["x"].data_ptr(), mu.ctypes.data, it.ctypes.data, inner.ctypes.data)
+        outs.append((mu, it, inner))
+    L.check(L.lib().deblur_solve_batch(ctx.handle, len(problems), reqs, C.byref(g), C.byref(o), 1,
+                                       _stream(stream)), ctx.handle)
+    return [dict(mu=list(mu), iters=[int(v) for v in it], inner=[int(v) for v in inner]) for (mu, it, inner) in outs]
+
+
 def deblur_solve_device(b_dev, psf_dev, m, S, x_dev, solver="irls", wavelet="haar", levels=2, transfer="X",
                         precision="fp32", ctx=None, stream=None, **options):
     """Same call on device buffers (torch float64 CUDA tensors, column-major)."""

@@ -1355,6 +1355,10 @@ struct BatchSolver {
 
   void run_gcvs(const std::vector<int>& need) {
     if (need.empty()) return;
+    // the GCV evaluations run on the worker streams and read what the main
+    // stream wrote last: a new level's right-hand side and auxiliaries
+    // (start_level), a newly admitted problem's hierarchy (add_problem)
+    CK(cudaStreamSynchronize(st));
     const int nw = std::min((int)wst.size(), (int)need.size());
     std::vector<std::thread> th;
     std::vector<DbError> errs(nw);
