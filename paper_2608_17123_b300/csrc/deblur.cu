@@ -275,6 +275,9 @@ struct Level {
   double* Bd_c = nullptr;
   Acc *br = nullptr, *bc = nullptr, *brT = nullptr, *bcT = nullptr;
   float* rho = nullptr;      // GCV symbol ratios [n]
+  int ntaps = 0;             // level 0 of a sparse non-separable PSF: direct taps (BandOp)
+  int* tap_pq = nullptr;
+  Acc* tap_w = nullptr;
   double* b64 = nullptr;     // right-hand side in double (levels that use the exact GCV)
   // vectors
   T* b = nullptr;
@@ -288,6 +291,7 @@ struct Level {
     BandOp<Acc> o;
     o.m = m; o.nterms = nterms; o.dlo = dlo; o.w = w;
     o.br = br; o.bc = bc; o.brT = brT; o.bcT = bcT;
+    o.ntaps = ntaps; o.tap_pq = tap_pq; o.tap_w = tap_w;
     return o;
   }
 };
@@ -437,6 +441,8 @@ struct Engine {
   size_t gn = 0;
 
   GcvBufs<Acc>* gcur = nullptr;      // the buffers in use (for the Krylov cache)
+  std::vector<Acc> host_taps;        // level-0 taps while their upload is in flight
+  std::vector<int> host_tap_pq;
   GcvBufs<Acc> own_bufs;
   uint64_t epoch = 0;                // unique per build (keys the Krylov cache)
 
@@ -513,6 +519,18 @@ struct Engine {
       fc = nfc;
     }
     H.nterms = nterms;
+    // non-zero taps of the PSF (column-major, psf[(p + R) + (q + R) S])
+    std::vector<int> tpq;
+    host_taps.clear();
+    for (int q = -(S / 2); q <= S / 2; ++q)
+      for (int p = -(S / 2); p <= S / 2; ++p) {
+        const double v = key[1 + (p + S / 2) + (size_t)(q + S / 2) * S];
+        if (v != 0.0) {
+          tpq.push_back(((p + 128) << 8) | (q + 128));
+          host_taps.push_back((Acc)v);
+        }
+      }
+    host_tap_pq = tpq;
     const Filter f = make_filter(wv);
     const int kmax = gram_dim(go);
     for (int i = 0; i < levels; ++i) {
@@ -528,6 +546,17 @@ struct Engine {
       L.br = A.take<Acc>(nb); L.bc = A.take<Acc>(nb); L.brT = A.take<Acc>(nb); L.bcT = A.take<Acc>(nb);
       const int gb = grid_for(nb, ctx->nsm);
       if (i == 0) {
+        // a non-separable PSF with few non-zero taps (a motion blur) is
+        // applied directly on level 0: fewer operations than its separable
+        // terms (about nterms * 3 * S per pixel)
+        const int nnz = (int)host_tap_pq.size();
+        if (nterms > 1 && nnz < nterms * 2 * S && nnz <= MAX_TAPS && nnz <= TM * band_pitch(L.w)) {
+          L.ntaps = nnz;
+          L.tap_pq = A.take<int>(nnz);
+          L.tap_w = A.take<Acc>(nnz);
+          CK(cudaMemcpyAsync(L.tap_pq, host_tap_pq.data(), nnz * sizeof(int), cudaMemcpyHostToDevice, st));
+          CK(cudaMemcpyAsync(L.tap_w, host_taps.data(), nnz * sizeof(Acc), cudaMemcpyHostToDevice, st));
+        }
         { count_launch(); k_fine_bands_d<<<gb, 256, 0, st>>>(L.m, S, nterms, fr, L.Bd_r); }
         { count_launch(); k_fine_bands_d<<<gb, 256, 0, st>>>(L.m, S, nterms, fc, L.Bd_c); }
       } else {

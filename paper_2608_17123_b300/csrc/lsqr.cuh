@@ -160,10 +160,12 @@ __device__ int lsqr_pass_F(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p,
       }
     }
   }
+  const bool taps = P.op.ntaps > 0;
   if (src) {
-    if (init) gather_tile<true, X, Acc>(P.x0, m, r0, c0, g, Acc(1), sx);
-    else gather_tile<true, T, Acc>(P.v, m, r0, c0, g, Acc(1), sx);
-    if (!cbr) load_bands<Acc>(P.op, false, 0, r0, c0, g, sbr, sbc);
+    if (init) gather_tile<true, X, Acc>(P.x0, m, r0, c0, g, Acc(1), sx, taps);
+    else gather_tile<true, T, Acc>(P.v, m, r0, c0, g, Acc(1), sx, taps);
+    if (taps) load_taps<Acc>(P.op, sbr, reinterpret_cast<int*>(sbc));
+    else if (!cbr) load_bands<Acc>(P.op, false, 0, r0, c0, g, sbr, sbc);
   }
   Acc Av[PIX] = {};
   if (src) tile_conv<Acc>(P.op, false, r0, c0, g, sx, sz, cbr ? cbr : sbr, cbc ? cbc : sbc, Av, true);
@@ -271,8 +273,10 @@ __device__ int lsqr_pass_B(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p,
       vo[j] = v;
     }
   }
-  gather_tile<true, T, Acc>(P.uA, m, r0, c0, g, Acc(1), sx);
-  if (!cbr) load_bands<Acc>(P.op, true, 0, r0, c0, g, sbr, sbc);
+  const bool taps = P.op.ntaps > 0;
+  gather_tile<true, T, Acc>(P.uA, m, r0, c0, g, Acc(1), sx, taps);
+  if (taps) load_taps<Acc>(P.op, sbr, reinterpret_cast<int*>(sbc));
+  else if (!cbr) load_bands<Acc>(P.op, true, 0, r0, c0, g, sbr, sbc);
   Acc At[PIX] = {};
   tile_conv<Acc>(P.op, true, r0, c0, g, sx, sz, cbr ? cbr : sbr, cbc ? cbc : sbc, At, true);
   if (wait_rel) {

@@ -35,7 +35,16 @@ struct BandOp {
   const Acc* bc;              // [t][m][w] column factors (act on c)
   const Acc* brT;
   const Acc* bcT;
+  // Level 0 of a PSF whose non-zero taps are fewer than the work of its
+  // separable terms (a motion blur): the zero-boundary convolution applied
+  // directly, (A X)(r, c) = sum_i w_i X(r - p_i, c - q_i), X = 0 outside.
+  // ntaps = 0: the separable bands above.
+  int ntaps = 0;
+  const int* tap_pq = nullptr;   // (p + 128) << 8 | (q + 128)
+  const Acc* tap_w = nullptr;
 };
+
+constexpr int MAX_TAPS = 961;   // taps of a 31 x 31 PSF
 
 __host__ __device__ inline int band_pitch(int w) { return w | 1; }
 
@@ -89,7 +98,7 @@ constexpr int GATHER_BATCH = 12;   // loads a thread keeps in flight per gather 
 // up to 23 wide) rather than one per element.
 template <bool CG, typename T, typename Acc>
 __device__ __forceinline__ void gather_tile(const T* __restrict__ X, int m, int r0, int c0,
-                                            const TileGeom& g, Acc scale, Acc* sx) {
+                                            const TileGeom& g, Acc scale, Acc* sx, bool zero_outside = false) {
   constexpr int NT = 32 * TY;
   const int tid = threadIdx.x + 32 * threadIdx.y;
   const int H = g.H, HH = H * H;
@@ -101,7 +110,8 @@ __device__ __forceinline__ void gather_tile(const T* __restrict__ X, int m, int 
 #pragma unroll
     for (int q = 0; q < GATHER_BATCH; ++q) {
       v[q] = Acc(0);
-      if (base + q * NT < HH) v[q] = gload<CG, T>(X + wrap(rb + rr, m) + (size_t)wrap(cb + cc, m) * m);
+      const bool in = !zero_outside || ((unsigned)(rb + rr) < (unsigned)m && (unsigned)(cb + cc) < (unsigned)m);
+      if (base + q * NT < HH && in) v[q] = gload<CG, T>(X + wrap(rb + rr, m) + (size_t)wrap(cb + cc, m) * m);
       rr += dr;
       cc += dc;
       if (rr >= H) { rr -= H; ++cc; }
@@ -114,8 +124,39 @@ __device__ __forceinline__ void gather_tile(const T* __restrict__ X, int m, int 
 
 template <typename T, typename Acc>
 __device__ __forceinline__ void load_tile(const T* __restrict__ X, int m, int r0, int c0,
-                                          const TileGeom& g, Acc scale, Acc* sx) {
-  gather_tile<false, T, Acc>(X, m, r0, c0, g, scale, sx);
+                                          const TileGeom& g, Acc scale, Acc* sx, bool zero_outside = false) {
+  gather_tile<false, T, Acc>(X, m, r0, c0, g, scale, sx, zero_outside);
+}
+
+// The direct taps of a sparse level-0 operator into shared memory (they take
+// the place of the band rows): weights in sw, packed offsets in spq.
+template <typename Acc>
+__device__ __forceinline__ void load_taps(const BandOp<Acc>& op, Acc* sw, int* spq) {
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  for (int i = tid; i < op.ntaps; i += 32 * TY) {
+    sw[i] = op.tap_w[i];
+    spq[i] = op.tap_pq[i];
+  }
+}
+
+// out[j] += (A x)(r, c) = sum_i w_i x(r - p_i, c - q_i) over the zero-filled
+// window in sx, or (A^T x)(r, c) = sum_i w_i x(r + p_i, c + q_i); taps from
+// load_taps (the caller synchronised after loading them).
+template <typename Acc>
+__device__ __forceinline__ void taps_conv(const BandOp<Acc>& op, bool tr, const TileGeom& g, const Acc* sx,
+                                          const Acc* sw, const int* spq, Acc (&out)[PIX]) {
+  const int H = g.H;
+  const int lr = (int)threadIdx.x - g.lo;
+  const int lc0 = pix_col(0) - g.lo;
+  const int sgn = tr ? -1 : 1;
+  for (int i = 0; i < op.ntaps; ++i) {
+    const Acc wv = sw[i];
+    const int pq = spq[i];
+    const int dp = sgn * ((pq >> 8) - 128), dq = sgn * ((pq & 255) - 128);
+    const Acc* base = sx + (lc0 - dq) * H + (lr - dp);
+#pragma unroll
+    for (int j = 0; j < PIX; ++j) out[j] += wv * base[j * H];
+  }
 }
 
 // Bands of term t for the tile's rows / columns into shared memory (loads of
@@ -234,6 +275,15 @@ template <typename Acc>
 __device__ __forceinline__ void tile_conv(const BandOp<Acc>& op, bool tr, int r0, int c0,
                                           const TileGeom& g, const Acc* sx, Acc* sz, Acc* sbr,
                                           Acc* sbc, Acc (&out)[PIX], bool first_loaded = false) {
+  if (op.ntaps > 0) {
+    if (!first_loaded) {
+      __syncthreads();
+      load_taps<Acc>(op, sbr, reinterpret_cast<int*>(sbc));
+    }
+    __syncthreads();
+    taps_conv<Acc>(op, tr, g, sx, sbr, reinterpret_cast<const int*>(sbc), out);
+    return;
+  }
   for (int t = 0; t < op.nterms; ++t) {
     if (!(t == 0 && first_loaded)) {
       __syncthreads();
@@ -266,7 +316,7 @@ __global__ void __launch_bounds__(256) k_blur(BandOp<Acc> op, int tr, const T* _
   for (int tile = blockIdx.x; tile < nt * nt; tile += gridDim.x) {
     const int r0 = (tile % nt) * TM, c0 = (tile / nt) * TN;
     __syncthreads();
-    load_tile<T, Acc>(X, m, r0, c0, g, scale, sx);
+    load_tile<T, Acc>(X, m, r0, c0, g, scale, sx, op.ntaps > 0);
     Acc out[PIX] = {};
     tile_conv<Acc>(op, tr != 0, r0, c0, g, sx, sz, sbr, sbc, out);
     const int r = r0 + threadIdx.x;
