@@ -40,6 +40,16 @@ DOCUMENTED = [
     # float32 variants of the same cases meet 1 %.
     (lambda t, q: t.startswith("gcv[fp64-") and t.endswith("-m16]") and q == "gamma", 0.03,
      "exact GCV of a 16 x 16 level in float64: cancelling unregularised residual"),
+    # The 128 x 128 coarsest level of the m = 512 SB / Db4 cases at 1 % noise:
+    # its projected GCV is far from converged in the subspace dimension (the
+    # oracle's doubling sequence gives gamma = 0.028, 1.66, 1.49 at k = 41, 81,
+    # 161), and the device's k = 161 minimiser lands 1.35 % below the
+    # oracle's. Emulating in the oracle the device's float32 Krylov basis,
+    # float32 G_D sums and float32 operator inputs moves it by at most 0.14 %,
+    # so the cause is not isolated. The reconstruction is unaffected: x within
+    # 3.2e-5 of the oracle and every iteration count equal.
+    (lambda t, q: t.startswith("m512[sb-db4-") and t.endswith("-0.01]") and q == "mu[2]", 0.02,
+     "unconverged projected GCV of the coarsest level of the SB / Db4 m = 512 cases"),
 ]
 
 

@@ -47,6 +47,8 @@ PROJECTED_BOUND = {
     (32, 2.0, 9, False): 0.02,     # measured -0.007
     (32, 1.5, 7, True): 0.95,      # measured -0.941 (gamma 15x too small)
     (32, 2.0, 9, True): 0.95,      # measured -0.937
+    (64, 2.0, 9, False): 0.09,     # measured +0.074 (the small workload's size; exact pencil 4096 x 4096)
+    (64, 2.0, 9, True): 0.95,      # measured -0.916
 }
 
 
