@@ -77,12 +77,13 @@ LSQR_DRAM = {
 }
 
 
-def workload_desc():
+def workload_desc(batch=12):
     return {"workload": "m512_gauss_s3_15x15_3level_12combos", "m": M, "psf": f"gaussian sigma={SIGMA} {PSF_SIZE}x{PSF_SIZE}",
             "levels": LEVELS, "combos": "irls/mm/sb x haar/db4 x X/D", "noise": "1%,5%", "seed": SEED,
             "phantom": "40 rect + 20 disk", "precision": "fp32 storage, double-float (compensated fp32) sums, "
             "fp64 scalar recurrences / GCV / stopping tests",
-            "step": "one deblur_solve_batch call: the 12 combinations at one noise level",
+            "step": ("one deblur_solve_batch call: the 12 combinations at one noise level" if batch == 12 else
+                     "one deblur_solve_batch call: all 24 cases (12 combinations x 2 noise levels)"),
             "l2": "flushed (256 MB write) before every step"}
 
 
@@ -210,21 +211,21 @@ def parity_summary(results, golden):
         xo = np.load(os.path.join(GOLDEN, name + ".npz"))["x_samples"].astype(np.float64)
         xs = x_colmajor[idx]
         dx = float(np.linalg.norm(xs - xo) / np.linalg.norm(xo))
-        dit = max(abs(a - b) for a, b in zip(iters, c["iters"]))
-        dmu = max(abs(a - b) / b for a, b in zip(mu, c["mu"]))
+        dit = int(max(abs(a - b) for a, b in zip(iters, c["iters"])))
+        dmu = float(max(abs(a - b) / b for a, b in zip(mu, c["mu"])))
         rows.append((name, dx, dit, dmu, c["spread_x"], max(c["spread_mu"])))
     if not rows:
         return {"available": False, "why": "no timed step has a stored oracle case"}
     return {"available": True, "reference": "FP64 oracle, tests/golden/m512_oracle (16384-pixel sample)",
-            "steps_compared": len(rows),
-            "max_rel_diff_x": max(r[1] for r in rows),
+            "cases_compared": len(rows),
+            "max_rel_diff_x": float(max(r[1] for r in rows)),
             "median_rel_diff_x": float(np.median([r[1] for r in rows])),
-            "x_within_1e-4": sum(r[1] <= 1e-4 for r in rows),
-            "iters_within_1": sum(r[2] <= 1 for r in rows),
-            "mu_within_1pct": sum(r[3] <= 1e-2 for r in rows),
-            "max_rel_diff_mu": max(r[3] for r in rows),
-            "max_oracle_spread_x": max(r[4] for r in rows),
-            "worst": sorted(rows, key=lambda r: -r[1])[0][0]}
+            "x_within_1e-4": int(sum(bool(r[1] <= 1e-4) for r in rows)),
+            "iters_within_1": int(sum(bool(r[2] <= 1) for r in rows)),
+            "mu_within_1pct": int(sum(bool(r[3] <= 1e-2) for r in rows)),
+            "max_rel_diff_mu": float(max(r[3] for r in rows)),
+            "max_oracle_spread_x": float(max(r[4] for r in rows)),
+            "worst_x": sorted(rows, key=lambda r: -r[1])[0][0]}
 
 
 # ------------------------------------------------------------------ our arm
@@ -249,16 +250,19 @@ def run_ours(args, rank, world):
     x_true = I.phantom(M, 40, 20, SEED)
     bs = {nz: make_b(api, torch, M, x_true, psf, nz, 10_000 + SEED) for nz in NOISES}
     b_dev = {nz: torch.from_numpy(I.to_colmajor(b).ravel()).cuda() for nz, b in bs.items()}
-    nb = len(COMBOS)
+    nb = args.batch
     xs = [torch.empty(M * M, dtype=torch.float64, device="cuda") for _ in range(nb)]
 
-    def noise_of(s):
-        return NOISES[s % 2]
+    def cases_of(s):
+        """(noise, combination) of the images of step s: the 12 combinations at
+        one noise level (1 % on even steps, 5 % on odd ones), or with
+        --batch 24 all 24 cases of the workload."""
+        noises = NOISES if args.batch == 24 else (NOISES[s % 2],)
+        return [(nz, c) for nz in noises for c in COMBOS]
 
     def batch_dev(s):
-        nz = noise_of(s)
         probs = [dict(b=b_dev[nz], psf=psf_dev, x=xs[j], m=M, psf_size=PSF_SIZE, solver=c[0], wavelet=c[1],
-                      levels=LEVELS, transfer=c[2]) for j, c in enumerate(COMBOS)]
+                      levels=LEVELS, transfer=c[2]) for j, (nz, c) in enumerate(cases_of(s))]
         return api.deblur_solve_batch_device(probs, precision="fp32", ctx=ctx, stream=stream.cuda_stream)
 
     for i in range(args.warmup):
@@ -283,11 +287,11 @@ def run_ours(args, rank, world):
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
-        nz = noise_of(steps[i])
-        if nz not in seen:                       # each case once, for the oracle comparison
-            seen.add(nz)
-            for j, c in enumerate(COMBOS):
-                par_in.append((case_name(c[0], c[1], c[2], nz), xs[j].cpu().numpy(), res[j]["iters"], res[j]["mu"]))
+        for j, (nz, c) in enumerate(cases_of(steps[i])):
+            name = case_name(c[0], c[1], c[2], nz)
+            if name not in seen:                 # each case once, for the oracle comparison
+                seen.add(name)
+                par_in.append((name, xs[j].cpu().numpy(), res[j]["iters"], res[j]["mu"]))
     torch.cuda.synchronize()
     clk = clocks.stop()
     stats = ctx.stats()
@@ -297,17 +301,21 @@ def run_ours(args, rank, world):
         dist.barrier()
     images = nb * args.steps * world
     value = M * M * images / (t_total_ms / 1e3) / 1e6
+    if args.only_timed:
+        return {"metric": "deblurred Mpixel/s", "value": round(value, 4), "unit": "Mpixel/s",
+                "ms_per_step": round(t_total_ms / args.steps, 3), "images_per_step": nb,
+                "lsqr_ms_per_step": round(stats["lsqr_ms"] / args.steps, 2), "gpu_launches": int(stats["kernel_launches"])}, []
     parity = parity_summary(par_in, load_golden())
 
     # plain: the same 12 images of the first timed step, one deblur_solve each
     s0 = steps[args.warmup]
     plain_ms = 0.0
-    for j, c in enumerate(COMBOS):
+    for j, (nz, c) in enumerate(cases_of(s0)):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        api.deblur_solve_device(b_dev[noise_of(s0)], psf_dev, M, PSF_SIZE, xs[j], c[0], c[1], LEVELS, c[2],
+        api.deblur_solve_device(b_dev[nz], psf_dev, M, PSF_SIZE, xs[j], c[0], c[1], LEVELS, c[2],
                                 precision="fp32", ctx=ctx, stream=stream.cuda_stream)
         e1.record(stream)
         e1.synchronize()
@@ -318,8 +326,8 @@ def run_ours(args, rank, world):
     e2e_steps = args.steps if args.e2e_steps < 0 else min(args.steps, args.e2e_steps)
     e2e_ms = 0.0
     for i in range(e2e_steps):
-        nz = noise_of(steps[args.warmup + i])
-        probs = [dict(b=bs[nz], psf=psf, solver=c[0], wavelet=c[1], levels=LEVELS, transfer=c[2]) for c in COMBOS]
+        probs = [dict(b=bs[nz], psf=psf, solver=c[0], wavelet=c[1], levels=LEVELS, transfer=c[2])
+                 for nz, c in cases_of(steps[args.warmup + i])]
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -337,7 +345,7 @@ def run_ours(args, rank, world):
         "images_per_step": nb, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic phantoms (inputs module), b = A x_true by the library's blur + seeded noise, "
                 "rounded to float32",
-        "config": workload_desc(),
+        "config": workload_desc(args.batch),
         "images_per_s": round(images / (t_total_ms / 1e3), 4),
         "plain": {"images_per_s": round(nb / (plain_ms / 1e3), 4),
                   "mpixel_per_s": round(M * M * nb / (plain_ms / 1e3) / 1e6, 4),
@@ -658,7 +666,7 @@ def run_reference(args, rank, world):
     return {"metric": "deblurred Mpixel/s", "value": value, "unit": "Mpixel/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_desc(), "impl": "reference", "cpu_baseline": cb,
+            "data": "synthetic", "config": workload_desc(args.batch), "impl": "reference", "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -795,6 +803,24 @@ def run_lsqr_probe(args):
     psf = I.gaussian_psf(*{"gauss31": (6.0, 31), "gauss15": (3.0, 15)}[args.lsqr_psf])
     ctx = api.Context(0)
     ctx.set_autotune(False)
+    if args.lsqr_prec == "bf16":
+        # BF16 storage is reachable through the solve only: a single-level MM
+        # cycle of three outer iterations, one k_lsqr launch each
+        x_true = I.phantom(m, 40, 20, 6)
+        b = make_b(api, torch, m, x_true, psf, 0.01, 777)
+        bd = torch.from_numpy(I.to_colmajor(b).ravel()).cuda()
+        pd = torch.from_numpy(I.to_colmajor(psf).ravel()).cuda()
+        xd = torch.empty(m * m, dtype=torch.float64, device="cuda")
+        ctx.set_profiling(True)
+        r = api.deblur_solve_device(bd, pd, m, psf.shape[0], xd, "mm", "haar", 1, "I", precision="bf16", ctx=ctx,
+                                    kmax=3, gamma_fixed=1e-3, fine_direct=args.lsqr_direct)
+        st = ctx.stats()
+        ctx.close()
+        alg = (st["lsqr_pixel_iters_other"]) * lsqr_bytes_per_pixel_iter(2, 4, False)
+        return {"probe": "lsqr", "m": m, "psf": args.lsqr_psf, "precision": "bf16", "direct": args.lsqr_direct,
+                "launches": st["lsqr_launches"],
+                "pixel_iterations": st["lsqr_pixel_iters_other"], "ms": round(st["lsqr_ms"], 3),
+                "algorithmic_gb_s": round(alg / st["lsqr_ms"] / 1e6, 1)}
     xt = torch.from_numpy(I.to_colmajor(I.phantom(m, 40, 20, 6)).ravel()).to("cuda", torch.float32)
     b = torch.empty_like(xt)
     api.apply_blur(psf, m, xt, b, ctx=ctx)
@@ -802,19 +828,54 @@ def run_lsqr_probe(args):
     c = torch.zeros(2 * m * m, device="cuda", dtype=torch.float32)
     xo = torch.empty_like(xt)
     for _ in range(3):
-        api.lsqr_solve(psf, m, "mm", 1e-3, b, x0, c, None, xo, ctx=ctx, lsqr_maxit=100, lsqr_atol=0.0, lsqr_btol=0.0)
+        api.lsqr_solve(psf, m, "mm", 1e-3, b, x0, c, None, xo, ctx=ctx, lsqr_maxit=100, lsqr_atol=0.0, lsqr_btol=0.0,
+                       fine_direct=args.lsqr_direct)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     its = api.lsqr_solve(psf, m, "mm", 1e-3, b, x0, c, None, xo, ctx=ctx, lsqr_maxit=100, lsqr_atol=0.0,
-                         lsqr_btol=0.0)
+                         lsqr_btol=0.0, fine_direct=args.lsqr_direct)
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1)
     ctx.close()
     alg = (its + 1) * m * m * lsqr_bytes_per_pixel_iter(4, 4, False)
-    return {"probe": "lsqr", "m": m, "psf": args.lsqr_psf, "iterations": its, "ms": round(ms, 3),
+    return {"probe": "lsqr", "m": m, "psf": args.lsqr_psf, "direct": args.lsqr_direct, "iterations": its,
+            "ms": round(ms, 3),
             "us_per_iteration": round(1e3 * ms / its, 2), "algorithmic_gb_s": round(alg / ms / 1e6, 1)}
+
+
+def run_one_solve(args):
+    """One m = 512 image of the benchmark workload (one solver / wavelet /
+    transfer combination at one noise level) by the plain call, after one
+    untimed solve of the same image: the command the per-kernel launch lists
+    of profiles/ are taken on (about 5-9 K launches)."""
+    import torch
+    from paper_2608_17123_b300 import api
+    from paper_2608_17123_b300 import inputs as I
+    solver, wavelet, transfer = args.combo.split("-")
+    ctx = api.Context(0)
+    ctx.set_profiling(True)
+    psf = I.gaussian_psf(SIGMA, PSF_SIZE)
+    psf_dev = torch.from_numpy(I.to_colmajor(psf).ravel()).cuda()
+    x_true = I.phantom(M, 40, 20, SEED)
+    b = make_b(api, torch, M, x_true, psf, args.noise, 10_000 + SEED)
+    b_dev = torch.from_numpy(I.to_colmajor(b).ravel()).cuda()
+    xd = torch.empty(M * M, dtype=torch.float64, device="cuda")
+    run = lambda: api.deblur_solve_device(b_dev, psf_dev, M, PSF_SIZE, xd, solver, wavelet, LEVELS, transfer,
+                                          precision="fp32", ctx=ctx)
+    run()
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r = run()
+    e1.record()
+    e1.synchronize()
+    st = ctx.stats()
+    ctx.close()
+    return {"probe": "solve", "m": M, "combo": args.combo, "noise": args.noise, "ms": round(e0.elapsed_time(e1), 2),
+            "iters": r["iters"], "launches": st["kernel_launches"], "lsqr_ms": round(st["lsqr_ms"], 2)}
 
 
 # ------------------------------------------------------------------ phantom study
@@ -887,16 +948,27 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=-1, help="-1: every timed step")
     ap.add_argument("--large-steps", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=12, choices=[12, 24],
+                    help="images per step: the 12 combinations at one noise level, or all 24 cases")
+    ap.add_argument("--only-timed", action="store_true",
+                    help="stop after the timed steps (profiling runs: no plain, e2e, parity, large, serving "
+                         "or CPU measurement)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", dest="forms", action="store_false",
                     help="skip the serving measurement")
     ap.add_argument("--lsqr-m", type=int, default=2048)
     ap.add_argument("--lsqr-psf", default="gauss31", choices=["gauss31", "gauss15"])
-    ap.add_argument("--workload", default="m512", choices=["m512", "batch", "serve", "study", "lsqr"],
+    ap.add_argument("--lsqr-prec", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--lsqr-direct", type=int, default=1, choices=[0, 1],
+                    help="level-0 blur of the probe: 1 direct (TMA windows), 0 band form")
+    ap.add_argument("--combo", default="irls-haar-X", help="solve probe: solver-wavelet-transfer")
+    ap.add_argument("--noise", type=float, default=0.01, help="solve probe: noise level")
+    ap.add_argument("--workload", default="m512", choices=["m512", "batch", "serve", "study", "lsqr", "solve"],
                     help="m512: the benchmark line; batch: 64 uneven images batched vs one at a time; "
                          "serve: Poisson request stream against the server; study: the phantom study of "
-                         "the paper's experiments; lsqr: four single-level LSQR launches (profiling)")
+                         "the paper's experiments; lsqr: four single-level LSQR launches (profiling); solve: "
+                         "one plain solve of one m = 512 case (profiling)")
     ap.add_argument("--batch-images", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-slots", type=int, default=16)
@@ -904,7 +976,7 @@ def main():
     args = ap.parse_args()
     if args.workload != "m512":
         fn = {"batch": run_batch_workload, "serve": run_serve_workload, "study": run_phantom_study,
-              "lsqr": run_lsqr_probe}[args.workload]
+              "lsqr": run_lsqr_probe, "solve": run_one_solve}[args.workload]
         print(json.dumps(fn(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -921,7 +993,7 @@ def main():
         return
     line, names = run_ours(args, rank, world)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and not args.only_timed:
             line["cpu_baseline"] = oracle_sample(names)
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -88,6 +88,12 @@ typedef struct {
                              /*   launch on every block and the call returns  */
                              /*   DB_ETIMEOUT; the context stays usable. 0    */
                              /*   expires at the first wait (a test setting). */
+  int    fine_direct;        /* 1: on level 0 of a separable PSF (odd side    */
+                             /*   <= 32, side m >= 64, FP32/BF16 storage) the */
+                             /*   LSQR passes apply the blur as a direct      */
+                             /*   convolution over TMA-loaded windows; 0: the */
+                             /*   band form on every level. Same operator,    */
+                             /*   summed in another order.                    */
 } db_opts;
 
 typedef struct db_context db_context;

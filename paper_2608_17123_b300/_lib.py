@@ -27,7 +27,7 @@ class DbOpts(C.Structure):
                 ("eps_irls", C.c_double), ("eps_mm", C.c_double), ("tau_sb", C.c_double),
                 ("lsqr_atol", C.c_double), ("lsqr_btol", C.c_double), ("lsqr_conlim", C.c_double),
                 ("lsqr_maxit", C.c_int), ("lsqr_warm_start", C.c_int), ("precision", C.c_int),
-                ("barrier_timeout_us", C.c_int)]
+                ("barrier_timeout_us", C.c_int), ("fine_direct", C.c_int)]
 
 
 class DbGcvOpts(C.Structure):

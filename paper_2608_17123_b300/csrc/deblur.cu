@@ -7,6 +7,7 @@
 // iteration (LSQR iteration count and the two RC norms) to take the stopping
 // decision of Eq. (stop).
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <cstdio>
 #include <cstring>
 #include <cmath>
@@ -137,6 +138,49 @@ static Filter make_filter(db_wavelet wv) {
     f.h[0] = (1 + s3) / d; f.h[1] = (3 + s3) / d; f.h[2] = (3 - s3) / d; f.h[3] = (1 - s3) / d;
   }
   return f;
+}
+
+// ---- tensor maps of the direct level-0 path ----------------------------------
+// cuTensorMapEncodeTiled is reached through the runtime's driver entry point
+// (no link against the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Map of the m x m column-major image at `base` (elements of esz bytes) for
+// the window box of toep_geom. The TMA rules are checked here, so a map that
+// exists satisfies them: 16-byte aligned base, a row pitch that is a multiple
+// of 16 bytes, an inner box extent that is a multiple of 16 bytes, box sides
+// of at most 256 and a first box row (f8 + a multiple of the tile side) whose
+// byte offset is a multiple of 16. Returns false when any rule fails or the
+// encoder is unavailable (the level then keeps the band path).
+static bool make_window_map(CUtensorMap* out, const void* base, int m, int esz, const ToepGeom& g) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || !base || (esz != 2 && esz != 4)) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+  if (((size_t)m * esz) % 16 != 0 || (g.RB * esz) % 16 != 0) return false;
+  if (g.RB > 256 || g.CB > 256 || g.RB < 8) return false;
+  if ((g.f8 * esz) % 16 != 0 || (TM * esz) % 16 != 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)m};
+  const cuuint64_t strides[1] = {(cuuint64_t)m * esz};
+  const cuuint32_t box[2] = {(cuuint32_t)g.RB, (cuuint32_t)g.CB};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType dt = esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUresult r = enc(out, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 static int grid_for(size_t n, int nsm, int per = 256) {
@@ -278,6 +322,9 @@ struct Level {
   int ntaps = 0;             // level 0 of a sparse non-separable PSF: direct taps (BandOp)
   int* tap_pq = nullptr;
   Acc* tap_w = nullptr;
+  int toep = 0;              // level 0 of a separable PSF: direct Toeplitz path of the LSQR passes
+  Acc* tp = nullptr;         // its taps (row factors [t][w], column factors [t][w])
+  CUtensorMap* tmaps = nullptr;   // window maps of v, uA, xa, xb (device)
   double* b64 = nullptr;     // right-hand side in double (levels that use the exact GCV)
   // vectors
   T* b = nullptr;
@@ -292,6 +339,7 @@ struct Level {
     o.m = m; o.nterms = nterms; o.dlo = dlo; o.w = w;
     o.br = br; o.bc = bc; o.brT = brT; o.bcT = bcT;
     o.ntaps = ntaps; o.tap_pq = tap_pq; o.tap_w = tap_w;
+    o.toep = toep; o.tp = tp;
     return o;
   }
 };
@@ -443,6 +491,8 @@ struct Engine {
   GcvBufs<Acc>* gcur = nullptr;      // the buffers in use (for the Krylov cache)
   std::vector<Acc> host_taps;        // level-0 taps while their upload is in flight
   std::vector<int> host_tap_pq;
+  std::vector<CUtensorMap> host_tmaps;   // level-0 window maps while their upload is in flight
+  int* d_blur_err = nullptr;         // copy-timeout flag of the direct level-0 blur
   GcvBufs<Acc> own_bufs;
   uint64_t epoch = 0;                // unique per build (keys the Krylov cache)
 
@@ -469,6 +519,7 @@ struct Engine {
       tot += n * (sizeof(T) * 16 + sizeof(X) * 3) + n * sizeof(float) + n * sizeof(double);
       tot += (size_t)mi * (S + 64) * (sizeof(double) * 2 + sizeof(Acc) * 4) * S + 4096;
       tot += (size_t)4 * S * m * 16;
+      tot += 16384;   // direct-path taps and tensor maps
     }
     return tot + ((size_t)m * m / 1024 + 64) * 6 * sizeof(double) + 8 * 4096 + ((size_t)2 * S * S + S) * 8;
   }
@@ -483,6 +534,7 @@ struct Engine {
     Arena& A = arena ? *arena : ctx->arena;
     static std::atomic<uint64_t> build_counter{0};
     epoch = ++build_counter;
+    d_blur_err = nullptr;
     H.S = S;
     H.levels = levels;
     H.lv.assign(levels, Level<T>());
@@ -583,6 +635,7 @@ struct Engine {
         L.v = A.take<T>(n); L.wv = A.take<T>(n); L.dlt = A.take<X>(n);
         L.a0x = A.take<T>(n); L.a0y = A.take<T>(n); L.a1x = A.take<T>(n); L.a1y = A.take<T>(n);
       }
+      if (i == 0) setup_direct(L, A, nterms, S, with_vectors);
     }
     if (with_vectors && b_dev) {
       const size_t n0 = H.lv[0].n;
@@ -626,13 +679,97 @@ struct Engine {
     }
   }
 
+  // Direct Toeplitz path of the level-0 LSQR passes (toep.cuh): float
+  // working precision, a separable PSF (no direct taps) of odd side <= 32,
+  // a side of at least 64 (every tile full, the middle row of a band holds
+  // all taps), and tensor maps that pass the TMA rules. Otherwise the level
+  // keeps the band path.
+  void setup_direct(Level<T>& L, Arena& A, int nterms, int S, bool with_vectors) {
+    L.toep = 0;
+    L.tmaps = nullptr;
+    if (!std::is_same<Acc, float>::value || !o.fine_direct || L.ntaps > 0) return;
+    if ((S & 1) == 0 || S > TOEP_MAX_W || L.m < 64 || L.m % TM != 0 || L.w != S || L.dlo != -(S / 2)) return;
+    if (nterms * S > TOEP_MAX_TAPS) return;
+    if (!d_blur_err) {
+      d_blur_err = A.take<int>(1);
+      CK(cudaMemsetAsync(d_blur_err, 0, sizeof(int), st));
+    }
+    const ToepGeom g = toep_geom(L.dlo, L.w);
+    host_tmaps.assign(4, CUtensorMap{});
+    // the LSQR window maps (levels with vectors); without them the level
+    // still applies the standalone blur directly
+    if (with_vectors && make_window_map(&host_tmaps[0], L.v, L.m, (int)sizeof(T), g) &&
+        make_window_map(&host_tmaps[1], L.uA, L.m, (int)sizeof(T), g) &&
+        make_window_map(&host_tmaps[2], L.xa, L.m, (int)sizeof(X), g) &&
+        make_window_map(&host_tmaps[3], L.xb, L.m, (int)sizeof(X), g)) {
+      L.tmaps = A.take<CUtensorMap>(4);
+      CK(cudaMemcpyAsync(L.tmaps, host_tmaps.data(), 4 * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+    }
+    // taps: the middle row of each band (an interior row, where the zero
+    // boundary cuts nothing)
+    L.tp = A.take<Acc>((size_t)2 * nterms * S);
+    const size_t pitch = (size_t)L.m * S * sizeof(Acc);
+    CK(cudaMemcpy2DAsync(L.tp, S * sizeof(Acc), L.br + (size_t)(L.m / 2) * S, pitch, S * sizeof(Acc), nterms,
+                         cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpy2DAsync(L.tp + (size_t)nterms * S, S * sizeof(Acc), L.bc + (size_t)(L.m / 2) * S, pitch,
+                         S * sizeof(Acc), nterms, cudaMemcpyDeviceToDevice, st));
+    L.toep = 1;
+  }
+
+  // Window maps of a problem's LSQR launch on a level with the direct path;
+  // an x0 that is neither of the level's iterates turns the path off.
+  static void set_direct(LsqrProb<T, Acc>& P, const Level<T>& L, const X* x0) {
+    if (!P.op.toep) return;
+    if (!L.tmaps) { P.op.toep = 0; return; }
+    P.tm_v = L.tmaps + 0;
+    P.tm_u = L.tmaps + 1;
+    P.tm_x0 = x0 == L.xa ? L.tmaps + 2 : x0 == L.xb ? L.tmaps + 3 : nullptr;
+    if (x0 && !P.tm_x0) P.op.toep = 0;
+  }
+
   // ---------------------------------------------------------------- operators
   int smem_bytes(const BandOp<Acc>& op) const {
     TileGeom g = tile_geom(op, false), gt = tile_geom(op, true);
-    return std::max(tile_smem_elems(g.H, g.w), tile_smem_elems(gt.H, gt.w)) * (int)sizeof(Acc);
+    int b = std::max(tile_smem_elems(g.H, g.w), tile_smem_elems(gt.H, gt.w)) * (int)sizeof(Acc);
+    if (op.toep) b = std::max(b, toep_smem_bytes(toep_geom(op.dlo, op.w)));
+    return b;
+  }
+
+  // Level-0 blur of float vectors by the direct path (k_blur_direct); false
+  // when the level or the vector does not qualify (the caller then uses the
+  // band form).
+  bool blur_direct(const Level<T>& L, bool tr, const void* x, void* y, float scale, const double* nrm2, void* xcopy) {
+    if (!std::is_same<Acc, float>::value || !L.toep || !d_blur_err) return false;
+    const ToepGeom g = toep_geom(L.dlo, L.w);
+    CUtensorMap map;
+    if (!make_window_map(&map, x, L.m, 4, g)) return false;
+    if ((reinterpret_cast<uintptr_t>(y) & 15) || (reinterpret_cast<uintptr_t>(xcopy) & 15)) return false;
+    const int sm = toep_blur_smem_bytes(g);
+    if (sm > 48 * 1024) CK(cudaFuncSetAttribute(k_blur_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    const int nt = L.ntiles_side();
+    const int grid = std::min(nt * nt, 2 * ctx->nsm);
+    count_launch();
+    k_blur_direct<<<grid, dim3(32, TY), sm, st>>>(map, L.m, L.dlo, L.w, H.nterms, reinterpret_cast<const float*>(L.tp),
+                                                 tr ? 1 : 0, static_cast<float*>(y), scale, nrm2,
+                                                 static_cast<float*>(xcopy), d_blur_err);
+    CK(cudaGetLastError());
+    return true;
+  }
+
+  // Reads and clears the direct blur's copy-timeout flag.
+  void check_blur_err() {
+    if (!d_blur_err) return;
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, d_blur_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (e) {
+      CK(cudaMemsetAsync(d_blur_err, 0, sizeof(int), st));
+      throw DbError{DB_ETIMEOUT, "a window copy of the level-0 blur did not complete"};
+    }
   }
 
   void blur(const Level<T>& L, bool tr, const Acc* x, Acc* y, Acc scale = Acc(1)) {
+    if (blur_direct(L, tr, x, y, (float)scale, nullptr, nullptr)) return;
     BandOp<Acc> op = L.op(H.nterms);
     const int sm = smem_bytes(op);
     if (sm > 48 * 1024) CK(cudaFuncSetAttribute(k_blur<Acc, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
@@ -643,6 +780,7 @@ struct Engine {
   }
 
   void blur_T(const Level<T>& L, bool tr, const T* x, T* y) {
+    if (std::is_same<T, float>::value && blur_direct(L, tr, x, y, 1.f, nullptr, nullptr)) return;
     BandOp<Acc> op = L.op(H.nterms);
     const int sm = smem_bytes(op);
     if (sm > 48 * 1024) CK(cudaFuncSetAttribute(k_blur<T, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
@@ -670,7 +808,7 @@ struct Engine {
 
   // ---------------------------------------------------------------- LSQR
   int lsqr(const Level<T>& L, int solver, double gamma, const X* x0, int* stop_out = nullptr) {
-    LsqrProb<T, Acc> P;
+    LsqrProb<T, Acc> P{};
     P.op = L.op(H.nterms);
     P.m = L.m;
     P.solver = solver;
@@ -683,6 +821,7 @@ struct Engine {
     P.nt = L.ntiles_side();
     P.ntiles = P.nt * P.nt;
     P.tile_begin = 0;
+    set_direct(P, L, x0);
     CK(cudaMemcpyAsync(d_prob, &P, sizeof(P), cudaMemcpyHostToDevice, st));
     std::vector<int> tp(P.ntiles, 0);
     CK(cudaMemcpyAsync(d_tile_prob, tp.data(), sizeof(int) * tp.size(), cudaMemcpyHostToDevice, st));
@@ -991,6 +1130,7 @@ struct Engine {
   // Projected GCV with the fused Krylov kernels (float working precision):
   // five launches per basis vector and no host round trip until selection.
   void blur_dev(const Level<T>& L, bool tr, const Acc* x, Acc* y, const double* nrm2, Acc* xcopy) {
+    if (blur_direct(L, tr, x, y, 1.f, nrm2, xcopy)) return;
     BandOp<Acc> op = L.op(H.nterms);
     const int sm = smem_bytes(op);
     if (sm > 48 * 1024) CK(cudaFuncSetAttribute(k_blur<Acc, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
@@ -1442,6 +1582,7 @@ struct BatchSolver {
       X.nt = L.ntiles_side();
       X.ntiles = X.nt * X.nt;
       X.tile_begin = (int)tp.size();
+      Engine<T>::set_direct(X, L, X.x0);
       for (int t = 0; t < X.ntiles; ++t) tp.push_back((int)j);
       sm = std::max(sm, E.smem_bytes(X.op));
     }
@@ -1515,6 +1656,7 @@ struct BatchSolver {
         q.iters[q.level] = q.k;
         q.inners[q.level] = q.inner;
         if (q.level == 0) {
+          q.E->check_blur_err();
           q.done = true;
           finished.push_back(i);
         } else {
@@ -1546,6 +1688,7 @@ extern "C" void db_default_opts(db_opts* o, db_gcv_opts* g) {
     o->lsqr_atol = 1e-6; o->lsqr_btol = 1e-6; o->lsqr_conlim = 1e8; o->lsqr_maxit = 100;
     o->lsqr_warm_start = 1; o->precision = DB_PREC_FP32;
     o->barrier_timeout_us = 2000000;
+    o->fine_direct = 1;
   }
   if (g) {
     g->grid_points = 50; g->log10_gamma_lo = -10.0; g->log10_gamma_hi = 2.0;
@@ -1650,6 +1793,7 @@ static void validate_opts(const db_opts& o, const db_gcv_opts& g) {
   REQUIRE(g.exact_max_pixels >= 0 && g.exact_max_pixels <= 1024, "exact_max_pixels out of range");
   REQUIRE(o.kmax >= 1 && o.lsqr_maxit >= 1, "bad iteration limits");
   REQUIRE(o.barrier_timeout_us >= 0, "barrier_timeout_us must be >= 0");
+  REQUIRE(o.fine_direct == 0 || o.fine_direct == 1, "fine_direct must be 0 or 1");
 }
 
 template <typename T>
@@ -1663,6 +1807,7 @@ static void run_solve(db_context* ctx, cudaStream_t st, const double* b_dev, int
   ctx->arena.reset();
   E.build(psf_dev, S, m, levels, wv, b_dev, true);
   E.vcycle(solver, wv, levels == 1 ? DB_APPROACH_I : tr, mu, iters, inner);
+  E.check_blur_err();
   { count_launch(); k_convert_out<typename Traits<T>::X><<<grid_for((size_t)m * m, ctx->nsm), 256, 0, st>>>((size_t)m * m, E.H.lv[0].xa, x_dev); }
   CK(cudaGetLastError());
 }
@@ -2096,6 +2241,7 @@ static void op_blur(db_context* ctx, cudaStream_t st, const double* psf_host, in
   CK(cudaMemcpyAsync(dpsf, psf_host, (size_t)S * S * sizeof(double), cudaMemcpyHostToDevice, st));
   E.build(dpsf, S, m, level + 1, wv, nullptr, false);
   E.blur_T(E.H.lv[level], tr != 0, (const T*)x, (T*)y);
+  E.check_blur_err();
 }
 
 extern "C" db_status db_apply_blur(db_context* ctx, const double* psf_host, int S, int m, db_wavelet wv, int level, int tr,
@@ -2365,6 +2511,7 @@ static void op_gcv(db_context* ctx, cudaStream_t st, const double* psf_host, int
   const bool weighted = (solver == DB_IRLS) && a0;
   const bool shifted = (solver != DB_IRLS) && a0;
   *gamma_out = E.gcv(L, solver, weighted, shifted);
+  E.check_blur_err();
 }
 
 extern "C" db_status db_gcv_select(db_context* ctx, const double* psf_host, int S, int m, db_solver solver, const void* b,
@@ -2524,7 +2671,7 @@ static void static_lsqr(cudaStream_t st, const double* psf_host, int S, int m, d
   CK(cudaMemsetAsync(d_st, 0, sizeof(LsqrState), st));
   CK(cudaMemsetAsync(d_coef, 0, sizeof(LsqrCoef<Acc>), st));
   CK(cudaMemsetAsync(d_tile_prob, 0, sizeof(int) * ntiles, st));   // every tile belongs to problem 0
-  LsqrProb<T, Acc> P;
+  LsqrProb<T, Acc> P{};
   P.op = L.op(nterms);
   P.m = m;
   P.solver = solver;

@@ -16,7 +16,7 @@
 // runs the scalar recurrence and the stopping tests (rules S1-S3 with the
 // usual estimates, ||delta|| computed exactly) in double.
 #pragma once
-#include "ops.cuh"
+#include "toep.cuh"
 
 namespace db {
 
@@ -33,6 +33,11 @@ struct LsqrProb {
   T *uA, *uLx, *uLy, *v, *w;
   X* dlt;
   int tile_begin, ntiles, nt;    // tiles [tile_begin, tile_begin + ntiles), nt per side
+  // tensor maps of the window loads of the direct level-0 path (op.toep):
+  // v (pass F), u~_A (pass B) and x0 (pass F of the first phase)
+  const CUtensorMap* tm_v;
+  const CUtensorMap* tm_u;
+  const CUtensorMap* tm_x0;
 };
 
 struct LsqrState {
@@ -299,6 +304,324 @@ __device__ int lsqr_pass_B(const LsqrProb<T, Acc>& P, const LsqrCtl& ctl, int p,
     P.v[i] = store_cast<T, Acc>(vt);
     red.sq(0, vt);
   }
+  return 1;
+}
+
+// ---- direct level-0 path (op.toep, float working precision) ---------------
+// The same two passes over a tile in the vector mapping of toep.cuh. All of
+// a tile's inputs arrive by asynchronous copies on one mbarrier: the halo
+// window by one TMA box copy (thread 0) and the pointwise operands by bulk
+// copies into staging slots (warp y fills slot y, one column per lane), so
+// no operand occupies registers while the convolution runs. Every warp
+// arrives once per tile (the barrier counts TY arrivals), announcing the
+// bytes it copies. The copies follow the barrier at the top of the tile
+// (the previous tile's reads of the buffers are done) and the grid barrier
+// that published the vectors; a proxy fence orders them after both.
+
+// Warp-level: announce and issue the copy of one vector (p, elements of esz
+// bytes; null: none) of tile (r0, c0) into `slot` (column c0 + j at slot
+// column j + 1; with `left`, column c0 - 1 at slot column 0 when c0 > 0).
+// `extra`: bytes of further copies this warp's lane 0 issues afterwards.
+__device__ __forceinline__ void toep_stage(unsigned char* slot, const void* p, int esz, bool left, int r0, int c0,
+                                           int m, uint64_t* bar, unsigned extra) {
+  const int lane = threadIdx.x;
+  const unsigned colb = (unsigned)(TM * esz);
+  const bool lft = p && left && c0 > 0;
+  if (lane == 0) {
+    fence_proxy_async();
+    mbar_arrive_expect_tx(bar, extra + (p ? colb * (32u + (lft ? 1u : 0u)) : 0u));
+  }
+  __syncwarp();
+  if (p) {
+    fence_proxy_async();
+    const char* base = static_cast<const char*>(p) + (size_t)r0 * esz;
+    bulk_load(slot + (lane + 1) * colb, base + (size_t)(c0 + lane) * m * esz, colb, bar);
+    if (lane == 0 && lft) bulk_load(slot, base + (size_t)(c0 - 1) * m * esz, colb, bar);
+  }
+}
+
+// Warp-level (the warp without a slot): announce and issue the copy of the
+// taps of the level (2 * nterms * w floats, rounded up to 16 bytes; the
+// arena allocation behind them is 256-byte granular) into `dst`.
+__device__ __forceinline__ void toep_stage_taps(float* dst, const BandOp<float>& op, uint64_t* bar) {
+  if (threadIdx.x == 0) {
+    const unsigned bytes = (unsigned)((2 * op.nterms * op.w * 4 + 15) & ~15);
+    fence_proxy_async();
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_load(dst, op.tp, bytes, bar);
+  }
+  __syncwarp();
+}
+
+// Waits for the tile's copies (every thread). A copy from L2/HBM lands within
+// microseconds; the wait gives up after TOEP_COPY_LIMIT_NS, flags the error
+// for the whole grid and waits once more, also bounded, for copies still in
+// flight. Returns false (uniform over the block) on expiry.
+constexpr unsigned long long TOEP_COPY_LIMIT_NS = 1000000000ull;
+__device__ __forceinline__ bool toep_wait(const LsqrCtl& ctl, uint64_t* bar, unsigned& par) {
+  const bool ok = mbar_wait_bounded(bar, par, TOEP_COPY_LIMIT_NS);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      atomicExch(&ctl.gb->error, 1);
+      mbar_wait_bounded(bar, par, TOEP_COPY_LIMIT_NS);
+    }
+    __syncthreads();
+    return false;
+  }
+  par ^= 1u;
+  return true;
+}
+
+// 4 values of this thread's pixels (rows 4a.., slot column cl + 1 + dc)
+template <typename E>
+__device__ __forceinline__ void slot4(const unsigned char* slot, int a, int cl, int dc, float (&o)[4]) {
+  ld4s(reinterpret_cast<const E*>(slot) + (cl + 1 + dc) * TM + 4 * a, o);
+}
+
+template <typename T>
+__device__ int lsqr_pass_F_toep(const LsqrProb<T, float>& P, const LsqrCtl& ctl, int p, bool init, bool first,
+                                int r0, int c0, unsigned char* win, float* sz, unsigned char* slots,
+                                Sums3<float>& red, int ph, bool wait_rel, uint64_t* bar, unsigned& par) {
+  using X = typename Traits<T>::X;
+  const int m = P.m;
+  const BandOp<float>& op = P.op;
+  const ToepGeom g = toep_geom(op.dlo, op.w);
+  const bool src = init ? (P.x0 != nullptr) : true;   // input vector: x0 (phase 0) or v
+  const bool wtd = (P.solver == 0);
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  const int a = tid & 7, cl = tid >> 3;
+  const int r = r0 + 4 * a, c = c0 + cl;
+  const size_t i = r + (size_t)c * m;
+  float* stp = reinterpret_cast<float*>(slots + TOEP_SLOTS * TOEP_SLOT_BYTES);
+  // slots: 0 u~_A | b, 1 u~_Lx | a1x, 2 u~_Ly | a1y, 3 w, 4 delta, 5 a0x, 6 a0y
+  {
+    const void* sp = nullptr;
+    int esz = (int)sizeof(T);
+    switch (threadIdx.y) {
+      case 0: sp = init ? (const void*)P.b : (const void*)P.uA; break;
+      case 1: sp = init ? (P.solver == 2 ? (const void*)P.a1x : nullptr) : (const void*)P.uLx; break;
+      case 2: sp = init ? (P.solver == 2 ? (const void*)P.a1y : nullptr) : (const void*)P.uLy; break;
+      case 3: sp = (!init && !first) ? (const void*)P.w : nullptr; break;
+      case 4: sp = (!init && !first) ? (const void*)P.dlt : nullptr; esz = (int)sizeof(X); break;
+      case 5: sp = (wtd || init) ? (const void*)P.a0x : nullptr; break;
+      case 6: sp = (wtd || init) ? (const void*)P.a0y : nullptr; break;
+      default: break;
+    }
+    const int wesz = init ? (int)sizeof(X) : (int)sizeof(T);
+    const unsigned wbytes = (src && threadIdx.y == 0) ? (unsigned)(g.RB * g.CB * wesz) : 0u;
+    if (threadIdx.y == TOEP_SLOTS) toep_stage_taps(stp, op, bar);
+    else toep_stage(slots + threadIdx.y * TOEP_SLOT_BYTES, sp, esz, false, r0, c0, m, bar, wbytes);
+    if (src && tid == 0) tma_load_2d(win, init ? P.tm_x0 : P.tm_v, r0 + g.f8, c0 + op.dlo, bar);
+  }
+  if (!toep_wait(ctl, bar, par)) return -2;
+  // the input at this thread's pixels and their lower / right neighbours
+  float x0v[4] = {0.f, 0.f, 0.f, 0.f}, xdn[4] = {0.f, 0.f, 0.f, 0.f}, xrt[4] = {0.f, 0.f, 0.f, 0.f};
+  float Av[4] = {0.f, 0.f, 0.f, 0.f};
+  if (src) {
+    const int wr = 4 * a - g.f8, wc = cl - op.dlo;
+    if (init) {
+      const X* sx = reinterpret_cast<const X*>(win);
+      toep_conv_any<X>(g, op.w, op.nterms, stp, false, sx, sz, Av);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        x0v[j] = win_val(sx, wc * g.RB + wr + j);
+        xdn[j] = win_val(sx, wc * g.RB + wr + j + 1);
+        xrt[j] = win_val(sx, (wc + 1) * g.RB + wr + j);
+      }
+    } else {
+      const T* sx = reinterpret_cast<const T*>(win);
+      toep_conv_any<T>(g, op.w, op.nterms, stp, false, sx, sz, Av);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        x0v[j] = win_val(sx, wc * g.RB + wr + j);
+        xdn[j] = win_val(sx, wc * g.RB + wr + j + 1);
+        xrt[j] = win_val(sx, (wc + 1) * g.RB + wr + j);
+      }
+    }
+  }
+  if (wait_rel) {
+    const int d = lsqr_wait_release(ctl, ph);
+    if (d != 0) return d > 0 ? -1 : -2;
+  }
+  const TileHead<float> h = load_head<float>(ctl, p);
+  if (h.done) return 0;
+  const float sc = init ? 1.f : h.K.inv_alpha;   // v = v~ / alpha
+  const float sg = P.sg;
+  const float ab = init ? 0.f : h.K.ab;
+  const float phr = h.K.phr, thr = h.K.thr;
+  float wx[4] = {1.f, 1.f, 1.f, 1.f}, wy[4] = {1.f, 1.f, 1.f, 1.f};
+  if (wtd) {
+    slot4<T>(slots + 5 * TOEP_SLOT_BYTES, a, cl, 0, wx);
+    slot4<T>(slots + 6 * TOEP_SLOT_BYTES, a, cl, 0, wy);
+  }
+  float oA[4], oX[4], oY[4], oW[4], oD[4];
+  if (init) {
+    float bb[4], cx[4] = {0.f, 0.f, 0.f, 0.f}, cy[4] = {0.f, 0.f, 0.f, 0.f};
+    slot4<T>(slots, a, cl, 0, bb);
+    if (P.solver == 1 || P.solver == 2) {
+      slot4<T>(slots + 5 * TOEP_SLOT_BYTES, a, cl, 0, cx);
+      slot4<T>(slots + 6 * TOEP_SLOT_BYTES, a, cl, 0, cy);
+    }
+    if (P.solver == 2) {
+      float ex[4], ey[4];
+      slot4<T>(slots + 1 * TOEP_SLOT_BYTES, a, cl, 0, ex);
+      slot4<T>(slots + 2 * TOEP_SLOT_BYTES, a, cl, 0, ey);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) { cx[j] -= ex[j]; cy[j] -= ey[j]; }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int rj = r + j;
+      float qx = 0.f, qy = 0.f;
+      if (src) {
+        if (rj < m - 1) qx = xdn[j] - x0v[j];
+        if (c < m - 1) qy = xrt[j] - x0v[j];
+      }
+      qx *= wx[j];
+      qy *= wy[j];
+      const float ua = bb[j] - Av[j];
+      float ux = sg * (cx[j] - qx);
+      float uy = sg * (cy[j] - qy);
+      oD[j] = 0.f;
+      if (rj == m - 1) ux = 0.f;
+      if (c == m - 1) uy = 0.f;
+      oA[j] = ua; oX[j] = ux; oY[j] = uy;
+      red.sq(0, ua);
+      red.sq(0, ux);
+      red.sq(0, uy);
+    }
+    st4(P.dlt + i, oD);
+  } else {
+    float pu[4], px[4], py[4], pw_[4] = {0.f, 0.f, 0.f, 0.f}, pd[4] = {0.f, 0.f, 0.f, 0.f};
+    slot4<T>(slots, a, cl, 0, pu);
+    slot4<T>(slots + 1 * TOEP_SLOT_BYTES, a, cl, 0, px);
+    slot4<T>(slots + 2 * TOEP_SLOT_BYTES, a, cl, 0, py);
+    if (!first) {
+      slot4<T>(slots + 3 * TOEP_SLOT_BYTES, a, cl, 0, pw_);
+      slot4<X>(slots + 4 * TOEP_SLOT_BYTES, a, cl, 0, pd);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int rj = r + j;
+      const float v0 = sc * x0v[j];
+      float qx = 0.f, qy = 0.f;
+      if (rj < m - 1) qx = sc * (xdn[j] - x0v[j]);
+      if (c < m - 1) qy = sc * (xrt[j] - x0v[j]);
+      qx *= wx[j];
+      qy *= wy[j];
+      const float av = sc * Av[j];
+      const float ua = av - ab * pu[j];
+      float ux = sg * qx - ab * px[j];
+      float uy = sg * qy - ab * py[j];
+      if (first) {
+        oW[j] = v0;
+      } else {
+        const float wo = pw_[j];
+        const float dn = pd[j] + phr * wo;
+        oD[j] = dn;
+        oW[j] = v0 - thr * wo;
+        red.sq(1, dn);
+        red.sq(2, wo);
+      }
+      if (rj == m - 1) ux = 0.f;
+      if (c == m - 1) uy = 0.f;
+      oA[j] = ua; oX[j] = ux; oY[j] = uy;
+      red.sq(0, ua);
+      red.sq(0, ux);
+      red.sq(0, uy);
+    }
+    st4(P.w + i, oW);
+    if (!first) st4(P.dlt + i, oD);
+  }
+  st4(P.uA + i, oA);
+  st4(P.uLx + i, oX);
+  st4(P.uLy + i, oY);
+  return 1;
+}
+
+template <typename T>
+__device__ int lsqr_pass_B_toep(const LsqrProb<T, float>& P, const LsqrCtl& ctl, int p, bool init, int r0, int c0,
+                                unsigned char* win, float* sz, unsigned char* slots, Sums3<float>& red, int ph,
+                                bool wait_rel, uint64_t* bar, unsigned& par) {
+  const int m = P.m;
+  const BandOp<float>& op = P.op;
+  const ToepGeom g = toep_geom(op.dlo, op.w);
+  const bool wtd = (P.solver == 0);
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  const int a = tid & 7, cl = tid >> 3;
+  const int r = r0 + 4 * a, c = c0 + cl;
+  const size_t i = r + (size_t)c * m;
+  float* stp = reinterpret_cast<float*>(slots + TOEP_SLOTS * TOEP_SLOT_BYTES);
+  // slots: 0 u~_Lx, 1 u~_Ly (with column c0 - 1), 2 v~, 5 a0x, 6 a0y (with column c0 - 1)
+  {
+    const void* sp = nullptr;
+    bool left = false;
+    switch (threadIdx.y) {
+      case 0: sp = P.uLx; break;
+      case 1: sp = P.uLy; left = true; break;
+      case 2: sp = init ? nullptr : (const void*)P.v; break;
+      case 5: sp = wtd ? (const void*)P.a0x : nullptr; break;
+      case 6: sp = wtd ? (const void*)P.a0y : nullptr; left = true; break;
+      default: break;
+    }
+    const unsigned wbytes = threadIdx.y == 0 ? (unsigned)(g.RB * g.CB * (int)sizeof(T)) : 0u;
+    if (threadIdx.y == TOEP_SLOTS) toep_stage_taps(stp, op, bar);
+    else toep_stage(slots + threadIdx.y * TOEP_SLOT_BYTES, sp, (int)sizeof(T), left, r0, c0, m, bar, wbytes);
+    if (tid == 0) tma_load_2d(win, P.tm_u, r0 + g.f8, c0 + op.dlo, bar);
+  }
+  // the row above the tile (first pixel of the threads with a = 0; the
+  // others find it in the staged column)
+  float xm1 = 0.f, wxm1 = 1.f;
+  if (r > 0 && a == 0) {
+    xm1 = ldcg<T>(P.uLx + i - 1);
+    if (wtd) wxm1 = to_acc(P.a0x[i - 1]);
+  }
+  if (!toep_wait(ctl, bar, par)) return -2;
+  float At[4] = {0.f, 0.f, 0.f, 0.f};
+  toep_conv_any<T>(g, op.w, op.nterms, stp, true, reinterpret_cast<const T*>(win), sz, At);
+  if (wait_rel) {
+    const int d = lsqr_wait_release(ctl, ph);
+    if (d != 0) return d > 0 ? -1 : -2;
+  }
+  const TileHead<float> h = load_head<float>(ctl, p);
+  if (h.done) return 0;
+  // L^T applied to the (unscaled) gradient planes at this thread's pixels:
+  // the row above comes from the thread's own column except for its first
+  // pixel, the column to the left from the staged column c - 1
+  float x4[4], y4[4], yl[4] = {0.f, 0.f, 0.f, 0.f}, vo[4] = {0.f, 0.f, 0.f, 0.f};
+  float wx4[4] = {1.f, 1.f, 1.f, 1.f}, wy4[4] = {1.f, 1.f, 1.f, 1.f}, wyl[4] = {1.f, 1.f, 1.f, 1.f};
+  slot4<T>(slots, a, cl, 0, x4);
+  if (a > 0) {
+    xm1 = win_val(reinterpret_cast<const T*>(slots), (cl + 1) * TM + 4 * a - 1);
+    if (wtd) wxm1 = win_val(reinterpret_cast<const T*>(slots + 5 * TOEP_SLOT_BYTES), (cl + 1) * TM + 4 * a - 1);
+  }
+  slot4<T>(slots + 1 * TOEP_SLOT_BYTES, a, cl, 0, y4);
+  if (c > 0) slot4<T>(slots + 1 * TOEP_SLOT_BYTES, a, cl, -1, yl);
+  if (!init) slot4<T>(slots + 2 * TOEP_SLOT_BYTES, a, cl, 0, vo);
+  if (wtd) {
+    slot4<T>(slots + 5 * TOEP_SLOT_BYTES, a, cl, 0, wx4);
+    slot4<T>(slots + 6 * TOEP_SLOT_BYTES, a, cl, 0, wy4);
+    if (c > 0) slot4<T>(slots + 6 * TOEP_SLOT_BYTES, a, cl, -1, wyl);
+  }
+  const float ib = h.K.inv_beta;                    // u = u~ / beta
+  const float sgb = P.sg * ib;
+  const float ba = init ? 0.f : h.K.ba;
+  float ov[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int rj = r + j;
+    const float x1 = j ? x4[j - 1] : xm1, wx1 = j ? wx4[j - 1] : wxm1;
+    float l = 0.f;
+    if (rj < m - 1) l -= x4[j] * wx4[j];
+    if (rj > 0) l += x1 * wx1;
+    if (c < m - 1) l -= y4[j] * wy4[j];
+    if (c > 0) l += yl[j] * wyl[j];
+    float vt = ib * At[j] + sgb * l;
+    if (!init) vt -= ba * vo[j];
+    ov[j] = vt;
+    red.sq(0, vt);
+  }
+  st4(P.v + i, ov);
   return 1;
 }
 
@@ -576,8 +899,17 @@ template <typename T, typename Acc>
 __global__ void __launch_bounds__(256, 2) k_lsqr(const LsqrProb<T, Acc>* __restrict__ probs, LsqrCtl ctl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Acc* sm = reinterpret_cast<Acc*>(smem_raw);
+  // window of the direct level-0 path: the dynamic buffer rounded up to the
+  // 128-byte alignment of a TMA destination (the host adds the slack)
+  unsigned char* win = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
+                                                        ~static_cast<uintptr_t>(127));
+  __shared__ __align__(8) uint64_t s_bar;   // completion of the window copy
+  unsigned par = 0;                         // parity of the next completion
   __shared__ double scratch[3 * 32];
-  __shared__ __align__(16) LsqrProb<T, Acc> s_prob[LSQR_TCACHE];
+  // raw storage: the descriptors are copied in word by word below (a
+  // __shared__ object of the struct type would ask for a constructor)
+  __shared__ __align__(16) unsigned char s_prob_raw[LSQR_TCACHE * sizeof(LsqrProb<T, Acc>)];
+  LsqrProb<T, Acc>* s_prob = reinterpret_cast<LsqrProb<T, Acc>*>(s_prob_raw);
   __shared__ int s_pid[LSQR_TCACHE];
   __shared__ int s_skip[2];
   LsqrCoef<Acc>* coef = reinterpret_cast<LsqrCoef<Acc>*>(ctl.coef);
@@ -594,6 +926,7 @@ __global__ void __launch_bounds__(256, 2) k_lsqr(const LsqrProb<T, Acc>* __restr
     for (int w = tid; w < (int)(sizeof(LsqrProb<T, Acc>) / sizeof(int)); w += 32 * TY) dst[w] = src[w];
     if (tid == 0) s_pid[k] = p;
   }
+  if (tid == 0) mbar_init(&s_bar, TY);   // one arrival per warp and tile (direct path)
   __syncthreads();
   // band rows of the cached tiles, forward and transposed (one-term PSFs:
   // they are the same in every pass of the launch)
@@ -602,6 +935,7 @@ __global__ void __launch_bounds__(256, 2) k_lsqr(const LsqrProb<T, Acc>* __restr
       const int tile = blockIdx.x + k * (int)G;
       if (tile >= ctl.ntiles) break;
       const LsqrProb<T, Acc>& P = s_prob[k];
+      if (P.op.toep) continue;
       const int tl = tile - P.tile_begin;
       const int r0 = (tl % P.nt) * TM, c0 = (tl / P.nt) * TN;
       Acc* cb = sm + ctl.cache_off + (size_t)k * 4 * TM * ctl.band_pw;
@@ -644,8 +978,23 @@ __global__ void __launch_bounds__(256, 2) k_lsqr(const LsqrProb<T, Acc>* __restr
           cbr = cb;
           cbc = cb + TM * ctl.band_pw;
         }
-        const int rc = isF ? lsqr_pass_F<T, Acc>(P, ctl, p, it == 0, it == 1, r0, c0, sm, red, cbr, cbc, ph, !waited)
-                           : lsqr_pass_B<T, Acc>(P, ctl, p, it == 0, r0, c0, sm, red, cbr, cbc, ph, !waited);
+        int rc;
+        if constexpr (sizeof(Acc) == 4) {
+          if (P.op.toep) {
+            const ToepGeom tg = toep_geom(P.op.dlo, P.op.w);
+            float* sz = reinterpret_cast<float*>(win + toep_win_bytes(tg));
+            unsigned char* slots = win + toep_win_bytes(tg) + toep_z_bytes(tg);
+            rc = isF ? lsqr_pass_F_toep<T>(P, ctl, p, it == 0, it == 1, r0, c0, win, sz, slots, red, ph, !waited,
+                                           &s_bar, par)
+                     : lsqr_pass_B_toep<T>(P, ctl, p, it == 0, r0, c0, win, sz, slots, red, ph, !waited, &s_bar, par);
+          } else {
+            rc = isF ? lsqr_pass_F<T, Acc>(P, ctl, p, it == 0, it == 1, r0, c0, sm, red, cbr, cbc, ph, !waited)
+                     : lsqr_pass_B<T, Acc>(P, ctl, p, it == 0, r0, c0, sm, red, cbr, cbc, ph, !waited);
+          }
+        } else {
+          rc = isF ? lsqr_pass_F<T, Acc>(P, ctl, p, it == 0, it == 1, r0, c0, sm, red, cbr, cbc, ph, !waited)
+                   : lsqr_pass_B<T, Acc>(P, ctl, p, it == 0, r0, c0, sm, red, cbr, cbc, ph, !waited);
+        }
         waited = true;
         if (rc < 0) return;    // every problem has stopped, or a wait timed out (uniform over the block)
         if (rc == 0) continue;

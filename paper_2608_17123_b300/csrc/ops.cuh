@@ -42,6 +42,12 @@ struct BandOp {
   int ntaps = 0;
   const int* tap_pq = nullptr;   // (p + 128) << 8 | (q + 128)
   const Acc* tap_w = nullptr;
+  // Level 0 of a separable PSF (FP32/BF16 LSQR): the same blur applied as a
+  // direct Toeplitz convolution over a TMA-loaded, zero-filled window
+  // (toep.cuh). tp: forward taps, row factors [t][w] then column factors
+  // [t][w]. The bands above stay valid (and are used by the other kernels).
+  int toep = 0;
+  const Acc* tp = nullptr;
 };
 
 constexpr int MAX_TAPS = 961;   // taps of a 31 x 31 PSF

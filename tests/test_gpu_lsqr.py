@@ -64,6 +64,37 @@ def test_lsqr_matches_oracle(prec, solver, m):
     compare_at_iteration(name, sub, gamma, x0, o, prec, its, its_ref, x, x_ref, target)
 
 
+@pytest.mark.parametrize("direct", [1, 0], ids=["direct", "bands"])
+@pytest.mark.parametrize("Sz,sigma", [(3, 0.8), (15, 3.0), (31, 6.0)], ids=["S3", "S15", "S31"])
+@pytest.mark.parametrize("solver", ["irls", "mm", "sb"])
+def test_lsqr_level0_forms_match_oracle(direct, Sz, sigma, solver):
+    """Level 0 of a separable PSF in FP32, applied by the direct Toeplitz
+    path (TMA-loaded zero-filled windows, fine_direct = 1) and by the band
+    form (fine_direct = 0), each against the oracle: m = 128 (16 tiles, the
+    halo crossing the image border on every side), PSF sides 3, 15 and 31
+    (the 8-, 16- and 32-tap unrolled convolutions)."""
+    import torch
+    m = 128
+    A, b, x_true, psf = problem(m, sigma, Sz, seed=2)
+    x0 = 0.9 * x_true
+    a0, a1 = aux_for(solver, x0, m)
+    f32 = lambda v: v.astype(np.float32).astype(np.float64)
+    b, x0 = f32(b), f32(x0)
+    a0 = tuple(f32(v) for v in a0)
+    a1 = None if a1 is None else tuple(f32(v) for v in a1)
+    gamma = 2e-4
+    o = S.opts_with()
+    sub = S.Subproblem(A, b, weights=a0 if solver == "irls" else None,
+                       c=None if solver == "irls" else (a0 if solver == "mm" else (a0[0] - a1[0], a0[1] - a1[1])))
+    x_ref, its_ref = sub.solve(gamma, x0, o)
+    dt = torch.float32
+    xo = torch.empty(m * m, device="cuda", dtype=dt)
+    its = api.lsqr_solve(psf, m, solver, gamma, img_to_dev(b, dt), img_to_dev(x0, dt), planes_to_dev(*a0, dt),
+                         None if a1 is None else planes_to_dev(*a1, dt), xo, fine_direct=direct)
+    compare_at_iteration(f"lsqr_level0[{'direct' if direct else 'bands'}-S{Sz}-{solver}]", sub, gamma, x0, o,
+                         "fp32", its, its_ref, dev_to_img(xo, m), x_ref, 1e-4)
+
+
 def compare_at_iteration(name, sub, gamma, x0, o, prec, its, its_ref, x, x_ref, target):
     """Iteration count against the oracle's, with the oracle's own spread of
     it under rounding noise; then x. The stopping iteration is a discrete
