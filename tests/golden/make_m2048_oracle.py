@@ -11,12 +11,16 @@ Daubechies-4 V-cycle (Alg. 4) of the given solver and transfer strategy
 
 Stored: gamma per level, outer and LSQR iteration counts per level, ||x||,
 x at 16384 fixed pixels (seed 2048), the error against the phantom and the
-wall time of the solve. There are no perturbed reruns at this size (one
-solve takes tens of minutes), so the comparison uses the stated targets.
+wall time of the solve. With --rerun SEED the same solve runs under the
+bfloat16 rounding-noise model of tests/perturb.py (bfloat16 unit roundoff on
+the LSQR operator outputs and the per-pixel planes, float32 inside GCV) and
+is stored beside it as <case>.rerun<SEED>.npz: the oracle's own spread under
+the storage precision of the GPU path. One solve takes about 1.5 h.
 
-This script calls only oracle/ and the input generator.
+This script calls only oracle/, the input generator and that noise model.
 
     python tests/golden/make_m2048_oracle.py mm X
+    python tests/golden/make_m2048_oracle.py mm X --rerun 12345
 """
 from __future__ import annotations
 
@@ -48,6 +52,7 @@ def main():
     from oracle import solvers as S
     from paper_2608_17123_b300 import inputs as I
     solver, transfer = sys.argv[1], sys.argv[2]
+    rerun = int(sys.argv[4]) if len(sys.argv) > 4 and sys.argv[3] == "--rerun" else None
     name = f"gauss31-{solver}-db4-{transfer}"
     os.makedirs(OUT, exist_ok=True)
     ip = os.path.join(OUT, "sample_index.npy")
@@ -61,6 +66,17 @@ def main():
     x_true = I.phantom(M, R, R // 2, SEED)
     b = to_bf16(I.add_noise(A.apply(x_true), I.noise_direction(M, 10_000 + SEED), NOISE))
     t0 = time.time()
+    if rerun is not None:
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from perturb import noisy
+        r = noisy(lambda: S.mgm(b, A, solver, "db4", LEVELS, transfer), "bf16", rerun)
+        wall = time.time() - t0
+        x = r["x"]
+        np.savez(os.path.join(OUT, f"{name}.rerun{rerun}.npz"), x_samples=x.T.reshape(-1)[idx].astype(np.float32),
+                 mu=np.array(r["mu"]), iters=np.array(r["iters"], dtype=np.int32),
+                 inner=np.array(r["inner"], dtype=np.int32), oracle_wall_s=np.float64(wall))
+        print(name, "rerun", rerun, f"{wall:.0f} s", r["iters"], r["mu"], flush=True)
+        return
     r = S.mgm(b, A, solver, "db4", LEVELS, transfer)
     wall = time.time() - t0
     x = r["x"]
