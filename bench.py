@@ -9,13 +9,14 @@ deblurred by 3-level V-cycles (Alg. 4) under all 12 combinations of
 dot products as double-float sums of exact products; scalar recurrences, GCV
 selection and stopping tests in FP64.
 
-One step = one batch: the 12 combinations of one noise level (1 % on even
-steps, 5 % on odd steps) in one deblur_solve_batch call on device buffers.
+One step = one batch: the 24 cases of the workload (the 12 combinations at
+both noise levels) in one deblur_solve_batch call on device buffers
+(--batch 12: the 12 combinations of one noise level, alternating).
 Metric: deblurred Mpixel/s (whole job, all ranks). Inputs are resident in
 HBM when the timed region starts; L2 is flushed (256 MB write) before every
 step, outside the CUDA-event pair that times it.
 
-Beside it on the same line: `plain` (the same 12 images, one deblur_solve
+Beside it on the same line: `plain` (the same images, one deblur_solve
 each), `e2e` (the same batches through the host-buffer call: copies in and
 out inside the timed region), `oracle_parity` (every case against the FP64
 oracle's stored result, tests/golden/m512_oracle), `serving` (the server
@@ -77,7 +78,7 @@ LSQR_DRAM = {
 }
 
 
-def workload_desc(batch=12):
+def workload_desc(batch=24):
     return {"workload": "m512_gauss_s3_15x15_3level_12combos", "m": M, "psf": f"gaussian sigma={SIGMA} {PSF_SIZE}x{PSF_SIZE}",
             "levels": LEVELS, "combos": "irls/mm/sb x haar/db4 x X/D", "noise": "1%,5%", "seed": SEED,
             "phantom": "40 rect + 20 disk", "precision": "fp32 storage, double-float (compensated fp32) sums, "
@@ -230,11 +231,12 @@ def parity_summary(results, golden):
 
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world):
-    """Timed steps: each step deblurs one batch -- the 512 x 512 phantom at one
-    noise level (1 % on even steps, 5 % on odd ones) under all 12
-    solver / wavelet / transfer combinations -- in one deblur_solve_batch
-    call on device buffers. The same 12 images one at a time (deblur_solve)
-    give the plain figures beside it."""
+    """Timed steps: each step deblurs one batch in one deblur_solve_batch call
+    on device buffers -- the 512 x 512 phantom under all 12 solver / wavelet /
+    transfer combinations at both noise levels (24 images, the default), or
+    with --batch 12 at one noise level (1 % on even steps, 5 % on odd ones).
+    The same images one at a time (deblur_solve) give the plain figures
+    beside it."""
     import torch
     from paper_2608_17123_b300 import api
     from paper_2608_17123_b300 import inputs as I
@@ -307,7 +309,7 @@ def run_ours(args, rank, world):
                 "lsqr_ms_per_step": round(stats["lsqr_ms"] / args.steps, 2), "gpu_launches": int(stats["kernel_launches"])}, []
     parity = parity_summary(par_in, load_golden())
 
-    # plain: the same 12 images of the first timed step, one deblur_solve each
+    # plain: the images of the first timed step, one deblur_solve each
     s0 = steps[args.warmup]
     plain_ms = 0.0
     for j, (nz, c) in enumerate(cases_of(s0)):
@@ -337,8 +339,9 @@ def run_ours(args, rank, world):
 
     peak, peak_kind = load_peaks()
     roofline = lsqr_roofline_all(stats, 4, 4, peak, peak_kind, t_total_ms, "m512",
-                                 note="batched launches over the 12 problems of a step, every level; the vectors "
-                                      "of 12 m = 512 cycles (~250 MB) exceed the 126 MB L2 only in part")
+                                 note=f"batched launches over the {nb} problems of a step, every level; the "
+                                      f"vectors of {nb} m = 512 cycles (~{21 * nb} MB) exceed the 126 MB L2 "
+                                      "only in part")
     line = {
         "metric": "deblurred Mpixel/s", "value": round(value, 4), "unit": "Mpixel/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_total_ms / args.steps, 3),
@@ -948,7 +951,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=-1, help="-1: every timed step")
     ap.add_argument("--large-steps", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=12, choices=[12, 24],
+    ap.add_argument("--batch", type=int, default=24, choices=[12, 24],
                     help="images per step: the 12 combinations at one noise level, or all 24 cases")
     ap.add_argument("--only-timed", action="store_true",
                     help="stop after the timed steps (profiling runs: no plain, e2e, parity, large, serving "

@@ -23,6 +23,7 @@
 #include <deque>
 #include <map>
 #include <chrono>
+#include <functional>
 
 #include "../../include/deblur.h"
 #include "gcv.cuh"
@@ -1394,6 +1395,61 @@ struct Engine {
 // batched solves: many V-cycles advanced together (one outer iteration of
 // every unfinished problem per scheduler step)
 // ============================================================================
+// Persistent worker threads of the batched solver's GCV evaluations: run(f,
+// n) calls f(0) .. f(n-1) on n workers and returns when all have returned.
+// Starting threads once per solve (not once per scheduler step) keeps the
+// step's fixed cost to a wake-up and a join.
+struct WorkerPool {
+  std::vector<std::thread> th;
+  std::mutex mu;
+  std::condition_variable cv, done;
+  std::function<void(int)> job;
+  unsigned gen = 0;
+  int active = 0, pending = 0;
+  bool stop = false;
+
+  void start(int n, int device) {
+    for (int w = 0; w < n; ++w)
+      th.emplace_back([this, w, device]() {
+        cudaSetDevice(device);
+        unsigned seen = 0;
+        for (;;) {
+          std::function<void(int)> f;
+          {
+            std::unique_lock<std::mutex> lk(mu);
+            cv.wait(lk, [&]() { return stop || gen != seen; });
+            if (stop) return;
+            seen = gen;
+            if (w >= active) continue;
+            f = job;
+          }
+          f(w);
+          {
+            std::lock_guard<std::mutex> lk(mu);
+            if (--pending == 0) done.notify_all();
+          }
+        }
+      });
+  }
+  void run(const std::function<void(int)>& f, int n) {
+    std::unique_lock<std::mutex> lk(mu);
+    job = f;
+    active = n;
+    pending = n;
+    ++gen;
+    cv.notify_all();
+    done.wait(lk, [&]() { return pending == 0; });
+  }
+  ~WorkerPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      stop = true;
+    }
+    cv.notify_all();
+    for (auto& t : th) t.join();
+  }
+};
+
 template <typename T>
 struct BatchSolver {
   using Acc = typename Traits<T>::Acc;
@@ -1420,6 +1476,7 @@ struct BatchSolver {
   db_gcv_opts go;
   std::vector<Prob> P;
   std::vector<cudaStream_t> wst;
+  std::unique_ptr<WorkerPool> pool;   // GCV workers (one per worker stream)
   LsqrProb<T, Acc>* d_probs = nullptr;
   LsqrState* d_states = nullptr;
   LsqrCoef<Acc>* d_coefs = nullptr;
@@ -1431,6 +1488,7 @@ struct BatchSolver {
 
   BatchSolver(db_context* c, cudaStream_t s) : ctx(c), st(s) {}
   ~BatchSolver() {
+    pool.reset();
     P.clear();
     for (auto w : wst) cudaStreamDestroy(w);
   }
@@ -1460,6 +1518,8 @@ struct BatchSolver {
     max_tiles = tiles;
     wst.resize(nworkers);
     for (int w = 0; w < nworkers; ++w) CK(cudaStreamCreateWithFlags(&wst[w], cudaStreamNonBlocking));
+    pool.reset(new WorkerPool());
+    pool->start(nworkers, ctx->device);
     d_probs = A.take<LsqrProb<T, Acc>>(max_probs);
     d_states = A.take<LsqrState>(max_probs);
     d_coefs = A.take<LsqrCoef<Acc>>(max_probs);
@@ -1529,34 +1589,32 @@ struct BatchSolver {
     // (start_level), a newly admitted problem's hierarchy (add_problem)
     CK(cudaStreamSynchronize(st));
     const int nw = std::min((int)wst.size(), (int)need.size());
-    std::vector<std::thread> th;
     std::vector<DbError> errs(nw);
     std::vector<int> failed(nw, 0);
-    for (int w = 0; w < nw; ++w) {
-      th.emplace_back([&, w]() {
-        CountScope cs(ctx);
-        try {
-          CK(cudaSetDevice(ctx->device));
-          // every problem has its own GCV buffers (and cached Krylov
-          // basis), so the evaluations are dealt to the workers in turn
-          for (size_t j = 0; j < need.size(); ++j) {
-            if ((int)(j % nw) != w) continue;
-            Prob& q = P[need[j]];
-            const int kind = gcv_kind(q);
-            q.E->adopt(q.gb);
-            q.E->st = wst[w];
-            // the level's x and auxiliaries were written on the main stream,
-            // which the scheduler has synchronised before this point
-            q.gamma = q.E->gcv(q.E->H.lv[q.level], q.solver, (kind - 1) & 1, ((kind - 1) & 2) != 0);
-            q.E->st = st;
-          }
-        } catch (DbError& e) {
-          errs[w] = e;
-          failed[w] = 1;
+    auto work = [&](int w) {
+      CountScope cs(ctx);
+      try {
+        // every problem has its own GCV buffers (and cached Krylov basis),
+        // so the evaluations are dealt to the workers in turn
+        for (size_t j = 0; j < need.size(); ++j) {
+          if ((int)(j % nw) != w) continue;
+          Prob& q = P[need[j]];
+          const int kind = gcv_kind(q);
+          q.E->adopt(q.gb);
+          q.E->st = wst[w];
+          // the level's x and auxiliaries were written on the main stream,
+          // which the scheduler has synchronised before this point
+          q.gamma = q.E->gcv(q.E->H.lv[q.level], q.solver, (kind - 1) & 1, ((kind - 1) & 2) != 0);
+          q.E->st = st;
         }
-      });
-    }
-    for (auto& t : th) t.join();
+      } catch (DbError& e) {
+        errs[w] = e;
+        failed[w] = 1;
+      }
+    };
+    // a single evaluation runs on the calling thread
+    if (nw == 1) work(0);
+    else pool->run(work, nw);
     for (int w = 0; w < nw; ++w)
       if (failed[w]) throw errs[w];
   }
