@@ -69,13 +69,26 @@ def lsqr_bytes_per_pixel_iter(elem, x_elem, irls):
     return 14 * elem + 2 * x_elem + (4 * elem if irls else 0)
 
 
-# DRAM bytes per k_lsqr launch from ncu captures (dram__bytes_read.sum +
-# dram__bytes_write.sum), to be retaken whenever k_lsqr changes; the scope
-# says which launch was captured.
+# DRAM bytes per LSQR pixel-iteration of k_lsqr from ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum of whole launches, divided by
+# their pixel-iterations; profiles/k_lsqr_dram_single_launch.md), to be
+# retaken whenever k_lsqr changes. The roofline's `traffic` is this figure
+# times the pixel-iterations of an average launch of the line; None where no
+# capture of the line's kind of launch exists. The scope says what was
+# captured.
 LSQR_DRAM = {
-    "m512": (None, "not captured for the current kernel"),
-    "large": (None, "not captured for the current kernel"),
+    "m512": (None, "not captured: the batched step cannot run under ncu (its cluster GCV launch fails there "
+                   "with 'too many resources requested'); a single-problem m = 512 launch (band form, earlier "
+                   "build) moved 0.17 B per pixel-iteration, its vectors iterating in L2"),
+    "large": (4.45, "scaled from three captured BF16 m = 2048 single-level LSQR launches of the direct path "
+                    "(0.050 GB read + 1.835 GB written per launch of 4.24e8 pixel-iterations = 4.45 B per "
+                    "pixel-iteration) to the pixel-iterations of an average finest-level launch"),
 }
+
+
+def lsqr_traffic(key, pixel_iters_per_launch):
+    per, scope = LSQR_DRAM[key]
+    return (None if per is None else round(per * pixel_iters_per_launch)), scope
 
 
 def workload_desc(batch=24):
@@ -383,7 +396,7 @@ def lsqr_roofline_all(stats, elem, x_elem, peak, peak_kind, t_total_ms, key, not
     launches = max(1, stats["lsqr_launches"])
     ms = stats["lsqr_ms"]
     achieved = (bytes_alg / launches) / ((ms / launches) / 1e3) / 1e9 if ms > 0 else 0.0
-    traffic, scope = LSQR_DRAM[key]
+    traffic, scope = lsqr_traffic(key, (stats["lsqr_pixel_iters_irls"] + stats["lsqr_pixel_iters_other"]) / launches)
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic, "traffic_scope": scope,
             "algorithmic_bytes_per_launch": round(bytes_alg / launches),
@@ -436,7 +449,8 @@ def lsqr_roofline(stats, elem, x_elem, peak, peak_kind, t_total_ms, key, note):
     launches = max(1, stats["lsqr_fine_launches"])
     ms = stats["lsqr_fine_ms"]
     achieved = (bytes_alg / launches) / ((ms / launches) / 1e3) / 1e9 if ms > 0 else 0.0
-    traffic, scope = LSQR_DRAM[key]
+    traffic, scope = lsqr_traffic(key, (stats["lsqr_fine_pixel_iters_irls"] + stats["lsqr_fine_pixel_iters_other"])
+                                  / launches)
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic, "traffic_scope": scope,
             "algorithmic_bytes_per_launch": round(bytes_alg / launches),
