@@ -295,7 +295,10 @@ db_status db_lsqr_solve(db_context* ctx, const double* psf_host, int psf_size, i
  * workspace does not fit (e.g. a high-rank PSF) returns DB_EINVAL with a
  * message in db_last_error(NULL); so do larger m or psf_size. Arguments,
  * layouts and results are those of db_lsqr_solve; b, x0 and the auxiliary
- * planes are read in place. The array is shared by every call on a device:
+ * planes are read in place. The blur is always applied in its band form
+ * (opts->fine_direct is not used: the direct path needs tensor maps in
+ * device memory), so the result equals db_lsqr_solve's with fine_direct = 0
+ * and differs from its direct-path result by float32 summation order. The array is shared by every call on a device:
  * calls that overlap in time race on it and must be serialised by the
  * caller. The first call on a device looks the array up; make it before any
  * stream capture begins. Synchronises `stream`, on success and on error

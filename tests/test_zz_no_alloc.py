@@ -1,6 +1,9 @@
 """db_lsqr_solve_static (no device allocation, static 16 MiB workspace)
-against db_lsqr_solve on the same inputs. Collected last so it also runs
-after every other GPU test in the same process."""
+against db_lsqr_solve on the same inputs, both in the band form of the blur
+(the static entry has no tensor maps, so it never takes the direct level-0
+path; the context call is asked for the same form with fine_direct = 0, so
+the two do the same arithmetic). Collected last so it also runs after every
+other GPU test in the same process."""
 import numpy as np
 import pytest
 
@@ -45,7 +48,7 @@ def test_static_matches_context_path(m, solver, prec):
     psf, (b, x0, a0, a1), dt = setup(m, solver, prec)
     gamma = 3e-4
     x_ref = torch.empty(m * m, device="cuda", dtype=dt)
-    its_ref = api.lsqr_solve(psf, m, solver, gamma, b, x0, a0, a1, x_ref)
+    its_ref = api.lsqr_solve(psf, m, solver, gamma, b, x0, a0, a1, x_ref, fine_direct=0)
     outs = []
     for _ in range(2):                       # two calls in a row
         xs = torch.empty(m * m, device="cuda", dtype=dt)
