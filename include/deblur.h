@@ -224,6 +224,11 @@ typedef struct {
   double   lsqr_fine_ms;
   double   lsqr_fine_pixel_iters_irls;
   double   lsqr_fine_pixel_iters_other;
+  /* LSQR solves (one per problem of a launch) whose level-0 blur took the
+   * direct path (db_opts.fine_direct), and launches of the direct
+   * standalone blur (GCV Krylov basis, db_apply_blur) */
+  uint64_t lsqr_direct_solves;
+  uint64_t blur_direct_launches;
 } db_stats;
 
 db_status db_set_profiling(db_context* ctx, int on);

@@ -41,7 +41,8 @@ class DbStats(C.Structure):
                 ("lsqr_pixel_iters_irls", C.c_double), ("lsqr_pixel_iters_other", C.c_double),
                 ("gcv_calls", C.c_uint64), ("outer_iterations", C.c_uint64), ("gcv_ms", C.c_double),
                 ("lsqr_fine_launches", C.c_uint64), ("lsqr_fine_ms", C.c_double),
-                ("lsqr_fine_pixel_iters_irls", C.c_double), ("lsqr_fine_pixel_iters_other", C.c_double)]
+                ("lsqr_fine_pixel_iters_irls", C.c_double), ("lsqr_fine_pixel_iters_other", C.c_double),
+                ("lsqr_direct_solves", C.c_uint64), ("blur_direct_launches", C.c_uint64)]
 
 
 class DbRequest(C.Structure):

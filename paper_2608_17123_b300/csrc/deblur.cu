@@ -92,7 +92,7 @@ struct db_context {
   Arena arena;
   std::string err;
   db_stats stats{};
-  std::atomic<uint64_t> n_launches{0}, n_gcv{0}, gcv_ns{0};
+  std::atomic<uint64_t> n_launches{0}, n_gcv{0}, gcv_ns{0}, n_blur_direct{0};
   // launch-shape autotuner: size class -> chosen shape (see lsqr_launch)
   int autotune = 1;
   std::mutex tune_mu;
@@ -750,6 +750,7 @@ struct Engine {
     const int nt = L.ntiles_side();
     const int grid = std::min(nt * nt, 2 * ctx->nsm);
     count_launch();
+    ctx->n_blur_direct.fetch_add(1, std::memory_order_relaxed);
     k_blur_direct<<<grid, dim3(32, TY), sm, st>>>(map, L.m, L.dlo, L.w, H.nterms, reinterpret_cast<const float*>(L.tp),
                                                  tr ? 1 : 0, static_cast<float*>(y), scale, nrm2,
                                                  static_cast<float*>(xcopy), d_blur_err);
@@ -823,6 +824,7 @@ struct Engine {
     P.ntiles = P.nt * P.nt;
     P.tile_begin = 0;
     set_direct(P, L, x0);
+    if (P.op.toep) ctx->stats.lsqr_direct_solves++;
     CK(cudaMemcpyAsync(d_prob, &P, sizeof(P), cudaMemcpyHostToDevice, st));
     std::vector<int> tp(P.ntiles, 0);
     CK(cudaMemcpyAsync(d_tile_prob, tp.data(), sizeof(int) * tp.size(), cudaMemcpyHostToDevice, st));
@@ -1641,6 +1643,7 @@ struct BatchSolver {
       X.ntiles = X.nt * X.nt;
       X.tile_begin = (int)tp.size();
       Engine<T>::set_direct(X, L, X.x0);
+      if (X.op.toep) ctx->stats.lsqr_direct_solves++;
       for (int t = 0; t < X.ntiles; ++t) tp.push_back((int)j);
       sm = std::max(sm, E.smem_bytes(X.op));
     }
@@ -1804,6 +1807,7 @@ extern "C" db_status db_get_stats(db_context* c, db_stats* out) {
   out->kernel_launches = c->n_launches.load();
   out->gcv_calls = c->n_gcv.load();
   out->gcv_ms = (double)c->gcv_ns.load() * 1e-6;
+  out->blur_direct_launches = c->n_blur_direct.load();
   return DB_OK;
 }
 
@@ -1813,6 +1817,7 @@ extern "C" db_status db_reset_stats(db_context* c) {
   c->n_launches = 0;
   c->n_gcv = 0;
   c->gcv_ns = 0;
+  c->n_blur_direct = 0;
   return DB_OK;
 }
 

@@ -195,3 +195,21 @@ def test_autotuned_shapes_give_identical_results(prec):
         ctx.close()
     assert outs[0][0] == outs[1][0]
     assert np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_direct_path_is_taken_and_can_be_turned_off():
+    """Level 0 of a separable PSF at m >= 64 in FP32 takes the direct path in
+    the LSQR solves and in the GCV Krylov blurs (counted in db_stats);
+    fine_direct = 0 turns it off, and a 32 x 32 level never takes it."""
+    A, b, _, psf = problem(128, 2.0, 9, seed=4)
+    counts = {}
+    for label, m, direct in (("on", 128, 1), ("off", 128, 0), ("small", 32, 1)):
+        bb = b if m == 128 else problem(32, 2.0, 9, seed=4)[1]
+        ctx = api.Context(0)
+        api.deblur_solve(bb, psf, "mm", "haar", 2, "X", precision="fp32", ctx=ctx, fine_direct=direct)
+        st = ctx.stats()
+        ctx.close()
+        counts[label] = (st["lsqr_direct_solves"], st["blur_direct_launches"], st["lsqr_launches"])
+    assert counts["on"][0] > 0 and counts["on"][1] > 0, counts
+    assert counts["off"][0] == 0 and counts["off"][1] == 0, counts
+    assert counts["small"][0] == 0 and counts["small"][1] == 0, counts
