@@ -939,8 +939,12 @@ struct Engine {
       cudaGetLastError();
       return false;
     }
+    // the last (largest) selection on a cluster of its own; with three, the
+    // two smaller ones share a second cluster, one after the other
+    const int ncl = na == 3 ? 2 : na;
+    const unsigned plan = na == 3 ? (0x4u | (0x3u << 4)) : (na == 2 ? (0x1u | (0x2u << 4)) : 0x1u);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(SCL_NC * na);
+    cfg.gridDim = dim3(SCL_NC * ncl);
     cfg.blockDim = dim3(SCL_THREADS);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = st;
@@ -957,7 +961,7 @@ struct Engine {
       return false;
     }
     count_launch();
-    CK(cudaLaunchKernelEx(&cfg, k_gcv_select_cl, as[0], as[na > 1 ? 1 : 0], as[na > 2 ? 2 : 0]));
+    CK(cudaLaunchKernelEx(&cfg, k_gcv_select_cl, as[0], as[na > 1 ? 1 : 0], as[na > 2 ? 2 : 0], plan));
     return true;
   }
 

@@ -1619,17 +1619,14 @@ __device__ void scl_reflector_warp(int len, const double* x, double* u, double* 
   if (lane == 0) *alpha_out = alpha;
 }
 
-__global__ void __launch_bounds__(SCL_THREADS) k_gcv_select_cl(GcvSelectArgs a0, GcvSelectArgs a1, GcvSelectArgs a2) {
+// One selection on the calling cluster (every thread of its SCL_NC CTAs).
+__device__ void sel_cl_run(const GcvSelectArgs& a) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) double sdyn[];
   __shared__ double sh[32 * 3];
   __shared__ double s_gam[SEL_MAXPTS], s_tr[SEL_MAXPTS], s_f[SEL_MAXPTS];
   __shared__ double s_bc[4];
-  const int sel = blockIdx.x / SCL_NC;
-  GcvSelectArgs a = a0;
-  if (sel == 1) a = a1;
-  else if (sel == 2) a = a2;
   const int rank = (int)cl.block_rank();
   const int K = a.kk, ld = a.ld, tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nwarp = nth >> 5;
@@ -1993,4 +1990,25 @@ __global__ void __launch_bounds__(SCL_THREADS) k_gcv_select_cl(GcvSelectArgs a0,
   }
 }
 
+
+// Up to three selections (k_gcv_select_cl args a0..a2) on gridDim.x /
+// SCL_NC clusters: cluster c runs, in index order, the selections whose bits
+// are set in bits [4c, 4c + 4) of `plan`. One cluster per selection gives
+// the lowest latency; two small selections back to back on one cluster take
+// about as long as one large one and leave the SMs to other work (the
+// batched solver runs several GCVs at once). The results do not depend on
+// the plan.
+__global__ void __launch_bounds__(SCL_THREADS) k_gcv_select_cl(GcvSelectArgs a0, GcvSelectArgs a1, GcvSelectArgs a2,
+                                                             unsigned plan) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned mask = (plan >> (4 * (blockIdx.x / SCL_NC))) & 15u;
+  bool first = true;
+  for (int q = 0; q < 3; ++q) {
+    if (!(mask & (1u << q))) continue;
+    if (!first) cl.sync();   // every CTA is done with the previous selection's shared memory
+    sel_cl_run(q == 0 ? a0 : (q == 1 ? a1 : a2));
+    first = false;
+  }
+}
 }  // namespace db
