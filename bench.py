@@ -69,26 +69,30 @@ def lsqr_bytes_per_pixel_iter(elem, x_elem, irls):
     return 14 * elem + 2 * x_elem + (4 * elem if irls else 0)
 
 
-# DRAM bytes per LSQR pixel-iteration of k_lsqr from ncu captures
-# (dram__bytes_read.sum + dram__bytes_write.sum of whole launches, divided by
-# their pixel-iterations; profiles/k_lsqr_dram_single_launch.md), to be
-# retaken whenever k_lsqr changes. The roofline's `traffic` is this figure
-# times the pixel-iterations of an average launch of the line; None where no
-# capture of the line's kind of launch exists. The scope says what was
-# captured.
+# DRAM traffic of k_lsqr from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum; profiles/k_lsqr_dram_single_launch.md and
+# profiles/k_lsqr_dram_bench_step.md), to be retaken whenever k_lsqr
+# changes: (kind, value, scope). "per_launch": bytes per launch measured on
+# the line's own command; "per_pixel_iteration": bytes per LSQR
+# pixel-iteration of a captured launch, times the pixel-iterations of an
+# average launch of the line.
 LSQR_DRAM = {
-    "m512": (None, "not captured: the batched step cannot run under ncu (its cluster GCV launch fails there "
-                   "with 'too many resources requested'); a single-problem m = 512 launch (band form, earlier "
-                   "build) moved 0.17 B per pixel-iteration, its vectors iterating in L2"),
-    "large": (4.45, "scaled from three captured BF16 m = 2048 single-level LSQR launches of the direct path "
-                    "(0.050 GB read + 1.835 GB written per launch of 4.24e8 pixel-iterations = 4.45 B per "
-                    "pixel-iteration) to the pixel-iterations of an average finest-level launch"),
+    "m512": ("per_launch", 1.2988e9,
+             "measured: the 150 k_lsqr launches of one timed step of this command (ncu, dram__bytes_read.sum + "
+             "dram__bytes_write.sum, 115.8 + 79.0 GB per step), averaged per launch; 28 % of their algorithmic "
+             "bytes, the rest served by L2"),
+    "large": ("per_pixel_iteration", 4.45,
+              "scaled from three captured BF16 m = 2048 single-level LSQR launches of the direct path "
+              "(0.050 GB read + 1.835 GB written per launch of 4.24e8 pixel-iterations = 4.45 B per "
+              "pixel-iteration) to the pixel-iterations of an average finest-level launch"),
 }
 
 
 def lsqr_traffic(key, pixel_iters_per_launch):
-    per, scope = LSQR_DRAM[key]
-    return (None if per is None else round(per * pixel_iters_per_launch)), scope
+    kind, val, scope = LSQR_DRAM[key]
+    if kind == "per_launch":
+        return round(val), scope
+    return round(val * pixel_iters_per_launch), scope
 
 
 def workload_desc(batch=24):

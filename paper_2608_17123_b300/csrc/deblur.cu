@@ -184,6 +184,35 @@ static bool make_window_map(CUtensorMap* out, const void* base, int m, int esz, 
   return r == CUDA_SUCCESS;
 }
 
+// Dynamic shared-memory limit of a kernel (cudaFuncAttributeMaxDynamic-
+// SharedMemorySize): a per-function, per-device setting that several host
+// threads (the batched solver's GCV workers, other contexts) change while
+// launching. It is only ever raised, under a lock, so a thread never lowers
+// it below what another thread is about to launch with. Returns false when
+// the device refuses the size.
+static std::mutex g_smem_attr_mu;
+static std::map<std::pair<int, const void*>, int> g_smem_attr;
+static bool raise_smem_limit(const void* kfn, int bytes) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  std::lock_guard<std::mutex> lk(g_smem_attr_mu);
+  int& cur = g_smem_attr[{dev, kfn}];
+  if (bytes <= cur) return true;
+  if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cur = bytes;
+  return true;
+}
+static void require_smem_limit(const void* kfn, int bytes) {
+  if (!raise_smem_limit(kfn, bytes))
+    throw DbError{DB_EINVAL, "kernel needs " + std::to_string(bytes) + " bytes of dynamic shared memory"};
+}
+
 static int grid_for(size_t n, int nsm, int per = 256) {
   size_t g = (n + per - 1) / per;
   size_t cap = (size_t)nsm * 8;
@@ -250,10 +279,10 @@ static void lsqr_launch(db_context* ctx, cudaStream_t st, const LsqrProb<T, Acc>
     c.cache_off = 0;
   }
   auto kfn = k_lsqr<T, Acc>;
-  // the opt-in limit is set to the exact size every time: static plus dynamic
-  // shared memory may pass the 48 KB default even when the dynamic part alone
-  // does not
-  CK(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  // the opt-in limit is raised on every launch, whatever the size: static
+  // plus dynamic shared memory may pass the 48 KB default even when the
+  // dynamic part alone does not
+  require_smem_limit((const void*)kfn, sm);
   int per_sm = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, sm));
   if (per_sm < 1) throw DbError{DB_EINVAL, "LSQR kernel does not fit on an SM (" + std::to_string(sm) +
@@ -746,7 +775,7 @@ struct Engine {
     if (!make_window_map(&map, x, L.m, 4, g)) return false;
     if ((reinterpret_cast<uintptr_t>(y) & 15) || (reinterpret_cast<uintptr_t>(xcopy) & 15)) return false;
     const int sm = toep_blur_smem_bytes(g);
-    if (sm > 48 * 1024) CK(cudaFuncSetAttribute(k_blur_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    if (sm > 48 * 1024) require_smem_limit((const void*)k_blur_direct, sm);
     const int nt = L.ntiles_side();
     const int grid = std::min(nt * nt, 2 * ctx->nsm);
     count_launch();
@@ -774,7 +803,7 @@ struct Engine {
     if (blur_direct(L, tr, x, y, (float)scale, nullptr, nullptr)) return;
     BandOp<Acc> op = L.op(H.nterms);
     const int sm = smem_bytes(op);
-    if (sm > 48 * 1024) CK(cudaFuncSetAttribute(k_blur<Acc, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    if (sm > 48 * 1024) require_smem_limit((const void*)k_blur<Acc, Acc>, sm);
     const int nt = L.ntiles_side();
     const int grid = std::min(nt * nt, ctx->nsm * 8);
     { count_launch(); k_blur<Acc, Acc><<<grid, dim3(32, TY), sm, st>>>(op, tr ? 1 : 0, x, y, scale); }
@@ -785,7 +814,7 @@ struct Engine {
     if (std::is_same<T, float>::value && blur_direct(L, tr, x, y, 1.f, nullptr, nullptr)) return;
     BandOp<Acc> op = L.op(H.nterms);
     const int sm = smem_bytes(op);
-    if (sm > 48 * 1024) CK(cudaFuncSetAttribute(k_blur<T, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    if (sm > 48 * 1024) require_smem_limit((const void*)k_blur<T, Acc>, sm);
     const int nt = L.ntiles_side();
     const int grid = std::min(nt * nt, ctx->nsm * 8);
     { count_launch(); k_blur<T, Acc><<<grid, dim3(32, TY), sm, st>>>(op, tr ? 1 : 0, x, y, Acc(1)); }
@@ -920,7 +949,7 @@ struct Engine {
     if (cluster) cluster = launch_select_cluster(as, na, kmax);
     if (!cluster) {
       const size_t sm = sel_smem_bytes(kmax);
-      CK(cudaFuncSetAttribute(k_gcv_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      require_smem_limit((const void*)k_gcv_select, (int)sm);
       { count_launch(); k_gcv_select<<<na, SEL_THREADS, sm, st>>>(as[0], as[na > 1 ? 1 : 0], as[na > 2 ? 2 : 0]); }
       CK(cudaGetLastError());
     }
@@ -935,10 +964,7 @@ struct Engine {
   // (nothing launched) when the device cannot hold such a cluster.
   bool launch_select_cluster(GcvSelectArgs* as, int na, int kmax) {
     const size_t sm = scl_layout(kmax).total * sizeof(double);
-    if (cudaFuncSetAttribute(k_gcv_select_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
+    if (!raise_smem_limit((const void*)k_gcv_select_cl, (int)sm)) return false;
     // the last (largest) selection on a cluster of its own; with three, the
     // two smaller ones share a second cluster, one after the other
     const int ncl = na == 3 ? 2 : na;
@@ -1140,7 +1166,7 @@ struct Engine {
     if (blur_direct(L, tr, x, y, 1.f, nrm2, xcopy)) return;
     BandOp<Acc> op = L.op(H.nterms);
     const int sm = smem_bytes(op);
-    if (sm > 48 * 1024) CK(cudaFuncSetAttribute(k_blur<Acc, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    if (sm > 48 * 1024) require_smem_limit((const void*)k_blur<Acc, Acc>, sm);
     const int nt = L.ntiles_side();
     const int grid = std::min(nt * nt, ctx->nsm * 8);
     { count_launch(); k_blur<Acc, Acc><<<grid, dim3(32, TY), sm, st>>>(op, tr ? 1 : 0, x, y, Acc(1), nrm2, xcopy); }
@@ -2763,7 +2789,7 @@ static void static_lsqr(cudaStream_t st, const double* psf_host, int S, int m, d
   TileGeom g0 = tile_geom(P.op, false), g1 = tile_geom(P.op, true);
   const int sm = std::max(tile_smem_elems(g0.H, g0.w), tile_smem_elems(g1.H, g1.w)) * (int)sizeof(Acc);
   auto kfn = k_lsqr<T, Acc>;
-  CK(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  require_smem_limit((const void*)kfn, sm);
   int per_sm = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, sm));
   REQUIRE(per_sm >= 1, "LSQR kernel does not fit on an SM");
