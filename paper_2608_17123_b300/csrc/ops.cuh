@@ -397,9 +397,9 @@ __global__ void k_restrict(int m, Filter f, const T* __restrict__ X, T* __restri
     int r = (int)(i % mc), c = (int)(i / mc);
     Acc s = 0;
     for (int b = 0; b < f.kappa; ++b) {
-      int cc = (2 * c + b) % m;
+      int cc = wrap(2 * c + b, m);
       Acc t = 0;
-      for (int a = 0; a < f.kappa; ++a) t += (Acc)f.h[a] * to_acc(X[(2 * r + a) % m + (size_t)cc * m]);
+      for (int a = 0; a < f.kappa; ++a) t += (Acc)f.h[a] * to_acc(X[wrap(2 * r + a, m) + (size_t)cc * m]);
       s += (Acc)f.h[b] * t;
     }
     Y[i] = store_cast<T, Acc>(s);
@@ -453,9 +453,9 @@ __global__ void k_coarsen_bands(int m, int dlo, int w, int nterms, Filter f,
     int s2 = wrap(r2 + dlo2 + k2, mc);
     double acc = 0.0;
     for (int a = 0; a < f.kappa; ++a) {
-      int ri = (2 * r2 + a) % m;
+      int ri = wrap(2 * r2 + a, m);
       for (int b = 0; b < f.kappa; ++b) {
-        int sj = (2 * s2 + b) % m;
+        int sj = wrap(2 * s2 + b, m);
         int kk = wrap(sj - ri - dlo, m);   // offset index within a period
         if (kk < w) acc += f.h[a] * f.h[b] * B[((size_t)t * m + ri) * w + kk];
       }
