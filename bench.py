@@ -648,9 +648,10 @@ def oracle_sample(names):
 
 def run_reference(args, rank, world):
     """The FP64 oracle on the host cores: step s times LSQR iterations on the
-    three level problems and one GCV call on level s mod 3 (a bounded sample
-    of the workload's solves); the Mpixel/s value scales the measured unit
-    costs by the oracle's recorded counts of the workload's cases."""
+    three level problems and one GCV call on level s mod 3 (the last step
+    also on any level no earlier step reached; a bounded sample of the
+    workload's solves); the Mpixel/s value scales the measured unit costs by
+    the oracle's recorded counts of the workload's cases."""
     if rank != 0:
         return None
     golden = load_golden()
@@ -664,8 +665,13 @@ def run_reference(args, rank, world):
     tg_acc = {l: [] for l in range(LEVELS)}
     t_steps = []
     for s in range(args.steps):
+        # the level of this step; the last step also takes every level no
+        # earlier step reached (runs of fewer than LEVELS steps)
+        lv = [s % LEVELS]
+        if s == args.steps - 1:
+            lv += [l for l in range(LEVELS) if not tg_acc[l] and l not in lv]
         t0 = time.perf_counter()
-        tl, tg = sample_unit_costs((s % LEVELS,))
+        tl, tg = sample_unit_costs(tuple(lv))
         t_steps.append(time.perf_counter() - t0)
         for l in range(LEVELS):
             tl_acc[l].append(tl[l])
