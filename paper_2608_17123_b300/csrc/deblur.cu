@@ -462,7 +462,9 @@ struct GcvBufs {
     ggA = A.take<double>(kmax);
     ggD = A.take<double>(kmax);
     gh = A.take<double>(kmax);
-    gwork_cap = (size_t)3 * kmax * kmax + (7 + 2 * SEL_MAXPTS + 8) * (size_t)kmax;
+    // three projected selections side by side (batched IRLS steps), or one
+    // selection of the largest basis (the exact mode's whole level)
+    gwork_cap = std::max((size_t)3 * kmax * kmax + (7 + 2 * SEL_MAXPTS + 8) * (size_t)kmax, sel_work_doubles(kmax));
     gwork = A.take<double>(gwork_cap);
     gAd = A.take<double>((size_t)std::max(exact_max, 1) * std::max(exact_max, 1));
     gbA = A.take<double>(kmax);
@@ -943,6 +945,8 @@ struct Engine {
     for (int i = 0; i < na; ++i) {
       as[i].trace_tab = tab;
       kmax = std::max(kmax, as[i].kk);
+      REQUIRE(as[i].work >= gwork && as[i].work + sel_work_doubles(as[i].kk) <= gwork + gwork_cap,
+              "GCV selection workspace too small");
     }
     bool cluster = true;
     for (int i = 0; i < na; ++i) cluster = cluster && !as[i].exact && as[i].kk <= SCL_MAXK;

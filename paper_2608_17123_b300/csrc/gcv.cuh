@@ -599,12 +599,14 @@ __device__ __forceinline__ double rsqrt_d(double x) {
   return y;
 }
 
-// Block sum of N doubles held by threads [0, nact); the other threads pass
-// zeros and skip the FP64 shuffles. Result in every thread. sh >= 32 N.
+// Block sum of N doubles over nact elements that the threads hold strided
+// (element i in thread i mod blockDim.x): only threads [0, min(nact,
+// blockDim.x)) hold values; the other threads pass zeros and skip the FP64
+// shuffles. Result in every thread. sh >= 32 N.
 template <int N>
 __device__ __forceinline__ void sel_sumN(double (&v)[N], int nact, double* sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nw = (nact + 31) >> 5;
+  const int nw = min((nact + 31) >> 5, (int)(blockDim.x >> 5));
   if (wid < nw) {
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = warp_sum(v[k]);

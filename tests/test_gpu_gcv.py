@@ -87,3 +87,48 @@ def test_gcv_exact_mode_tiny_level(prec, kind):
     g = api.gcv_select(psf, 8, "mm", img_to_dev(b, dt), None if a0 is None else planes_to_dev(*a0, dt))
     tol = 1e-6 if prec == "fp64" else 1e-2
     check(f"gcv_exact[{prec}-{kind}-m8]", "gamma", abs(g - g_ref) / g_ref, tol, spread, detail=(g, g_ref))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind", ["plain", "irls", "mm", "sb"])
+def test_gcv_exact_mode_m32(prec, kind):
+    """32 x 32 level (1024 pixels, the largest exact level the options allow)
+    with the exact mode on both sides (Sec. 3: the GCV function of the whole
+    pencil, trace from its eigenvalues). Here the projected rule would be off
+    by 0.2 % (plain), 15 % (MM) and 85 % (IRLS), so the test tells the two
+    modes apart. FP64: both sides stop Brent's search within tolx = 1e-5 in
+    log10 gamma, so they agree to 2 * ln(10) * 1e-5 < 1e-4 relative."""
+    import torch
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    m = 32
+    A, b, x_true, psf = problem(m)
+    qx, qy = O.L_apply(0.8 * x_true + 0.02)
+    a0 = a1 = None
+    if kind == "irls":
+        a0 = S.irls_weights(qx, qy, 0.03)
+    elif kind == "mm":
+        a0 = S.mm_surrogate(qx, qy, 0.03)
+    elif kind == "sb":
+        a0 = (S.shrink(qx, 0.005), S.shrink(qy, 0.005))
+        a1 = (0.5 * (qx - a0[0]), 0.5 * (qy - a0[1]))
+    rnd = (lambda v: v.astype(np.float32).astype(np.float64)) if prec == "fp32" else (lambda v: v)
+    b = rnd(b)
+    a0 = None if a0 is None else tuple(rnd(v) for v in a0)
+    a1 = None if a1 is None else tuple(rnd(v) for v in a1)
+    if kind == "irls":
+        sub = S.Subproblem(A, b, weights=a0)
+    elif kind == "mm":
+        sub = S.Subproblem(A, b, c=a0)
+    elif kind == "sb":
+        sub = S.Subproblem(A, b, c=(a0[0] - a1[0], a0[1] - a1[1]))
+    else:
+        sub = S.Subproblem(A, b)
+    o = S.opts_with(gcv_exact_max_n=1024)
+    g_ref = sub.gcv(o)
+    spread = max(abs(noisy(lambda: sub.gcv(o), prec, seed) - g_ref) / g_ref for seed in (12345, 777, 4242))
+    solver = {"plain": "mm", "irls": "irls", "mm": "mm", "sb": "sb"}[kind]
+    g = api.gcv_select(psf, m, solver, img_to_dev(b, dt),
+                       None if a0 is None else planes_to_dev(*a0, dt),
+                       None if a1 is None else planes_to_dev(*a1, dt), exact_max_pixels=1024)
+    tol = 1e-4 if prec == "fp64" else 1e-2
+    check(f"gcv_exact[{prec}-{kind}-m32]", "gamma", abs(g - g_ref) / g_ref, tol, spread, detail=(g, g_ref))
