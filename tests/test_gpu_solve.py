@@ -91,3 +91,31 @@ def test_solve_rejects_bad_arguments():
         api.deblur_solve(np.zeros((16, 16)), np.ones((4, 4)) / 16)   # even PSF
     with pytest.raises(DeblurError):
         api.deblur_solve(np.zeros((16, 16)), np.ones((3, 3)) / 9, "mm", "db4", 4, "X")  # coarsest 2 < 4 taps
+
+
+EXACT_COMBOS = [("irls", "haar", 2, "X"), ("mm", "db4", 2, "X"), ("sb", "haar", 2, "D"), ("mm", "haar", 1, "X")]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("combo", EXACT_COMBOS, ids=["-".join(map(str, c)) for c in EXACT_COMBOS])
+def test_solve_exact_gcv_m32(prec, combo):
+    """The V-cycle with the exact GCV (Sec. 3) on every level, the 32 x 32
+    finest one included (exact_max_pixels = 1024 on the device,
+    gcv_exact_max_n = 1024 in the oracle). On this image the projected rule
+    would move the finest gamma by 10x under IRLS and x by 8 %.
+
+    The spread adds one more rerun to the three noisy ones: the oracle with
+    Brent's tolerance ten times tighter (1e-6 in log10 gamma). The GCV
+    minimiser is located only to that tolerance, and here it alone moves the
+    oracle's FP64 IRLS x by 1.6e-6, above the FP64 target of 1e-6."""
+    A, b, _, psf = case(32, 1.5, 7, 6, 3, 1, 0.01)
+    bs = storage_rounded(b, prec)
+    o = S.opts_with(gcv_exact_max_n=1024)
+    key = ("ref-exact", id(A), combo, prec)
+    if key not in _CACHE:
+        _CACHE[key] = (S.mgm(bs, A, *combo, o=o),
+                       [noisy(lambda: S.mgm(bs, A, *combo, o=o), prec, seed) for seed in PERTURB_SEEDS] +
+                       [S.mgm(bs, A, *combo, o=S.opts_with(gcv_exact_max_n=1024, gcv_tolx=1e-6))])
+    r0, r1 = _CACHE[key]
+    r = api.deblur_solve(bs, psf, *combo, precision=prec, exact_max_pixels=1024)
+    check_solve(f"solve_exact_m32[{prec}-{'-'.join(map(str, combo))}]", r, r0, r1, XTOL[prec], rel)
