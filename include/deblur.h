@@ -68,7 +68,10 @@ typedef struct {
   int    proj_dim_max;       /* 160                                           */
   double gamma_fixed;        /* > 0: skip GCV and use this gamma everywhere   */
   int    exact_max_pixels;   /* 256: levels with at most this many pixels use */
-                             /*   the exact GCV (dense pair, exact trace)     */
+                             /*   the exact GCV (dense pair, exact trace);    */
+                             /*   0..1024, else DB_EINVAL. One block factors  */
+                             /*   the dense pencil of each selection in FP64: */
+                             /*   its cost grows as n^3 in the level's pixels */
 } db_gcv_opts;
 
 typedef struct {
