@@ -84,6 +84,23 @@ def test_gcv_exact_factors_equal_brute_force(kind):
         assert abs(F(gamma) - ref) <= 1e-7 * ref
 
 
+@pytest.mark.parametrize("kind", ["weighted", "shifted"])
+def test_gcv_exact_factors_equal_brute_force_m32(kind):
+    """The same pin on a 32 x 32 level (n = 1024), the largest level the
+    exact rule is run on: the factored GCV function against the plain
+    definition n ||A x_gamma - b||^2 / (n - tr(influence))^2 from dense solves."""
+    A, b, _ = small_problem(m=32, sigma=1.5, S_=7)
+    m = A.m
+    rng = np.random.default_rng(32)
+    w = S.irls_weights(*O.L_apply(rng.random((m, m))), 0.03) if kind == "weighted" else None
+    c = (rng.standard_normal((m - 1, m)) * 0.05, rng.standard_normal((m, m - 1)) * 0.05) if kind == "shifted" else None
+    _, _, Ad, Dd, cv = dense_subproblem(A, b, 1.0, w, c)
+    F = G.factors_exact(Ad, Dd, O.vec(b), cv if c is not None else None, m * m)
+    for gamma in [1e-5, 1e-3, 0.1]:
+        ref = brute_gcv(Ad, Dd, O.vec(b), cv, gamma)
+        assert abs(F(gamma) - ref) <= 1e-7 * ref
+
+
 def test_gcv_selection_matches_brute_grid():
     A, b, _ = small_problem(m=8, noise=0.05)
     _, _, Ad, Dd, cv = dense_subproblem(A, b, 1.0)
